@@ -1,0 +1,255 @@
+"""FP64 CPU oracle of the CMP / CRS semblance search (arXiv:1907.11678).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg may import this package; the product path (the CUDA library and
+its Python binding) never does.  The arithmetic lives in ``seis_oracle.c`` (plain C,
+FP64, OpenMP over output rows); this module compiles it with gcc and marshals numpy
+arrays into it.  It shares no code with the CUDA implementation.
+
+Pins (tests/test_oracle.py): closed forms and invariants of Eq. 1 (constant traces,
+a single trace, zero data, Cauchy-Schwarz bounds), an exactly-sampled hyperbolic
+event and an exactly-sampled dipping plane (S = 1 at the true operator), a
+hand-derived worked example under tests/golden/, a pure-Python brute force on tiny
+inputs, numpy.interp for the stack of a single trace, the CRS -> CMP reductions and
+central finite differences of the gradient.  The refinement (reading c16) is pinned
+only by its invariants (monotone S, bounds respected), so its result is
+"parity unpinned" beyond them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "seis_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libseis_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_vp = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -fopenmp); returns the shared-library path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.seis_oracle_cmp.restype = ctypes.c_int
+            lib.seis_oracle_crs.restype = ctypes.c_int
+            lib.seis_oracle_crs_eval.restype = ctypes.c_int
+            lib.seis_oracle_crs_refine.restype = ctypes.c_int
+            lib.seis_oracle_neighbours.restype = ctypes.c_int
+            lib.seis_oracle_max_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def max_threads() -> int:
+    return int(_load().seis_oracle_max_threads())
+
+
+def velocity_grid(vmin: float, vmax: float, nc: int) -> np.ndarray:
+    """Section 3.2: nc velocities linearly spaced in [vmin, vmax]; returns C = 4/v^2 (FP64)."""
+    out = np.empty(nc, np.float64)
+    _load().seis_oracle_velocity_grid(ctypes.c_double(vmin), ctypes.c_double(vmax),
+                                      ctypes.c_int32(nc), _p(out))
+    return out
+
+
+def linear_grid(lo: float, hi: float, n: int) -> np.ndarray:
+    out = np.empty(n, np.float64)
+    _load().seis_oracle_linear_grid(ctypes.c_double(lo), ctypes.c_double(hi),
+                                    ctypes.c_int32(n), _p(out))
+    return out
+
+
+class Result(dict):
+    """Attribute access to the oracle's output arrays."""
+    __getattr__ = dict.__getitem__
+
+
+def cmp_semblance(ds, C, w=11, rows=None, want_cube=True, knot_eps=1e-3, nthreads=0) -> Result:
+    """CMP search (Eq. 1, Algorithm 1, Section 3.2) on dataset ``ds`` (dict of arrays:
+    traces, trace_off, h, gather_off, out_off, dt).  ``rows``: global output rows to
+    evaluate (default all).  Returns S [nrows, nc], N, edge, best_idx, best_S,
+    second_S, stack (FP64 / int)."""
+    lib = _load()
+    traces = _c(ds["traces"], np.float32)
+    trace_off = _c(ds["trace_off"], np.int64)
+    h = _c(ds["h"], np.float32)
+    gather_off = _c(ds["gather_off"], np.int64)
+    out_off = _c(ds["out_off"], np.int64)
+    dt = _c(ds["dt"], np.float32)
+    C = _c(C, np.float32)
+    G = len(gather_off) - 1
+    nc = len(C)
+    rows_a = None if rows is None else _c(rows, np.int64)
+    nrows = int(out_off[-1]) if rows is None else len(rows_a)
+    S = np.empty((nrows, nc), np.float64) if want_cube else None
+    N = np.empty((nrows, nc), np.int32) if want_cube else None
+    edge = np.empty((nrows, nc), np.int8) if want_cube else None
+    bi = np.empty(nrows, np.int32)
+    bs = np.empty(nrows, np.float64)
+    b2 = np.empty(nrows, np.float64)
+    st = np.empty(nrows, np.float64)
+    rc = lib.seis_oracle_cmp(_p(traces), _p(trace_off), _p(h), _p(gather_off), _p(out_off),
+                             _p(dt), ctypes.c_int64(G), _p(C), ctypes.c_int32(nc),
+                             ctypes.c_int32(w), _p(rows_a), ctypes.c_int64(nrows),
+                             _p(S), _p(N), _p(edge), _p(bi), _p(bs), _p(b2), _p(st),
+                             ctypes.c_double(knot_eps), ctypes.c_int32(nthreads))
+    if rc != 0:
+        raise ValueError("seis_oracle_cmp: invalid arguments")
+    return Result(S=S, N=N, edge=edge, best_idx=bi, best_S=bs, second_S=b2, stack=st)
+
+
+def neighbours(ds, central, apm):
+    """CRS aperture (Section 2.2, Section 3.5): traces whose midpoint lies within apm of
+    the central gather's midpoint.  Returns (nbr_off int64 [n+1], nbr_trace int32, m_c f32)."""
+    lib = _load()
+    m = _c(ds["m"], np.float32)
+    gather_off = _c(ds["gather_off"], np.int64)
+    central = _c(central, np.int32)
+    G = len(gather_off) - 1
+    n = len(central)
+    off = np.empty(n + 1, np.int64)
+    mc = np.empty(n, np.float32)
+    rc = lib.seis_oracle_neighbours(_p(m), _p(gather_off), ctypes.c_int64(G), _p(central),
+                                    ctypes.c_int64(n), ctypes.c_double(apm), _p(off), None, _p(mc))
+    if rc != 0:
+        raise ValueError("seis_oracle_neighbours: invalid arguments")
+    tr = np.empty(int(off[-1]), np.int32)
+    lib.seis_oracle_neighbours(_p(m), _p(gather_off), ctypes.c_int64(G), _p(central),
+                               ctypes.c_int64(n), ctypes.c_double(apm), _p(off), _p(tr), _p(mc))
+    return off, tr, mc
+
+
+def _crs_common(ds, nb):
+    off, tr, mc, out_off_c, dt_c = nb
+    return (_c(ds["traces"], np.float32), _c(ds["trace_off"], np.int64), _c(ds["h"], np.float32),
+            _c(ds["m"], np.float32), _c(off, np.int64), _c(tr, np.int32), _c(mc, np.float32),
+            _c(out_off_c, np.int64), _c(dt_c, np.float32))
+
+
+def crs_semblance(ds, nb, A, B, C, w=11, rows=None, want_cube=False, knot_eps=1e-3,
+                  nthreads=0) -> Result:
+    """CRS search over the flattened grid cand = (ia*nB + ib)*nC + ic.  ``nb`` =
+    (nbr_off, nbr_trace, m_c, out_off_c, dt_c) describes the central CDPs."""
+    lib = _load()
+    arrs = _crs_common(ds, nb)
+    A = _c(A, np.float32); B = _c(B, np.float32); C = _c(C, np.float32)
+    ncen = len(arrs[6])
+    ncand = len(A) * len(B) * len(C)
+    rows_a = None if rows is None else _c(rows, np.int64)
+    nrows = int(arrs[7][-1]) if rows is None else len(rows_a)
+    S = np.empty((nrows, ncand), np.float64) if want_cube else None
+    N = np.empty((nrows, ncand), np.int32) if want_cube else None
+    edge = np.empty((nrows, ncand), np.int8) if want_cube else None
+    bi = np.empty(nrows, np.int32)
+    bs = np.empty(nrows, np.float64)
+    b2 = np.empty(nrows, np.float64)
+    st = np.empty(nrows, np.float64)
+    rc = lib.seis_oracle_crs(*[_p(a) for a in arrs], ctypes.c_int64(ncen),
+                             _p(A), ctypes.c_int32(len(A)), _p(B), ctypes.c_int32(len(B)),
+                             _p(C), ctypes.c_int32(len(C)), ctypes.c_int32(w),
+                             _p(rows_a), ctypes.c_int64(nrows),
+                             _p(S), _p(N), _p(edge), _p(bi), _p(bs), _p(b2), _p(st),
+                             ctypes.c_double(knot_eps), ctypes.c_int32(nthreads))
+    if rc != 0:
+        raise ValueError("seis_oracle_crs: invalid arguments")
+    return Result(S=S, N=N, edge=edge, best_idx=bi, best_S=bs, second_S=b2, stack=st)
+
+
+def crs_eval(ds, nb, theta, w=11, rows=None, nthreads=0) -> Result:
+    """S, dS/d(A,B,C) and stack at one operator per row (theta [nrows, 3])."""
+    lib = _load()
+    arrs = _crs_common(ds, nb)
+    ncen = len(arrs[6])
+    rows_a = None if rows is None else _c(rows, np.int64)
+    nrows = int(arrs[7][-1]) if rows is None else len(rows_a)
+    theta = _c(theta, np.float64).reshape(nrows, 3)
+    S = np.empty(nrows, np.float64)
+    grad = np.empty((nrows, 3), np.float64)
+    st = np.empty(nrows, np.float64)
+    N = np.empty(nrows, np.int32)
+    rc = lib.seis_oracle_crs_eval(*[_p(a) for a in arrs], ctypes.c_int64(ncen), ctypes.c_int32(w),
+                                  _p(rows_a), ctypes.c_int64(nrows), _p(theta),
+                                  _p(S), _p(grad), _p(st), _p(N), ctypes.c_int32(nthreads))
+    if rc != 0:
+        raise ValueError("seis_oracle_crs_eval: invalid arguments")
+    return Result(S=S, grad=grad, stack=st, N=N)
+
+
+def crs_refine(ds, nb, theta0, lo3, hi3, steps=20, step0=0.05, w=11, rows=None,
+               nthreads=0) -> Result:
+    """Projected normalised-gradient ascent from theta0 (reading c16)."""
+    lib = _load()
+    arrs = _crs_common(ds, nb)
+    ncen = len(arrs[6])
+    rows_a = None if rows is None else _c(rows, np.int64)
+    nrows = int(arrs[7][-1]) if rows is None else len(rows_a)
+    theta0 = _c(theta0, np.float64).reshape(nrows, 3)
+    lo3 = _c(lo3, np.float64); hi3 = _c(hi3, np.float64)
+    th = np.empty((nrows, 3), np.float64)
+    S = np.empty(nrows, np.float64)
+    grad = np.empty((nrows, 3), np.float64)
+    st = np.empty(nrows, np.float64)
+    rc = lib.seis_oracle_crs_refine(*[_p(a) for a in arrs], ctypes.c_int64(ncen),
+                                    ctypes.c_int32(w), _p(rows_a), ctypes.c_int64(nrows),
+                                    _p(theta0), _p(lo3), _p(hi3), ctypes.c_int32(steps),
+                                    ctypes.c_double(step0), _p(th), _p(S), _p(grad), _p(st),
+                                    ctypes.c_int32(nthreads))
+    if rc != 0:
+        raise ValueError("seis_oracle_crs_refine: invalid arguments")
+    return Result(theta=th, S=S, grad=grad, stack=st)
+
+
+def cmp_as_crs(ds, gathers=None):
+    """Neighbour description that makes each gather its own CRS 'aperture' (dm = 0
+    when all traces of a gather share one midpoint); used by the reduction tests."""
+    gather_off = np.asarray(ds["gather_off"], np.int64)
+    G = len(gather_off) - 1
+    gathers = np.arange(G) if gathers is None else np.asarray(gathers)
+    off = [0]
+    tr = []
+    for g in gathers:
+        ids = np.arange(gather_off[g], gather_off[g + 1], dtype=np.int32)
+        tr.append(ids)
+        off.append(off[-1] + len(ids))
+    m = np.asarray(ds["m"], np.float32)
+    mc = np.array([m[gather_off[g]] for g in gathers], np.float32)
+    out_off = np.asarray(ds["out_off"], np.int64)
+    ns = np.array([out_off[g + 1] - out_off[g] for g in gathers], np.int64)
+    out_off_c = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    dt_c = np.asarray(ds["dt"], np.float32)[gathers]
+    return (np.array(off, np.int64), np.concatenate(tr) if tr else np.zeros(0, np.int32),
+            mc, out_off_c, dt_c)

@@ -1,0 +1,498 @@
+/*
+ * seis_oracle.c -- plain, slow, FP64 CPU oracle of the CMP / CRS semblance search.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and its
+ * Python binding) may link, import or call this file.  It is used by the test suite,
+ * by the smoke check and by the benchmark's CPU-baseline leg, and by nothing else.
+ * It shares no code, header, table or helper with the CUDA implementation.
+ *
+ * What it computes (paper: "Massively Scaling Seismic Processing on Sunway TaihuLight
+ * Supercomputer", arXiv:1907.11678):
+ *
+ *   - Section 2.1 / Eq. 1: for every output time sample t0 = n*dt of a gather and every
+ *     candidate stacking parameter, intersect each trace with the traveltime curve,
+ *     linearly interpolate the amplitude there, and form the windowed semblance
+ *         S = sum_j (sum_i v_ij)^2 / (N * sum_j sum_i v_ij^2)
+ *     with N the number of traces that take part (the paper prints Eq. 1 without the
+ *     1/N factor; with it S lies in [0,1]).
+ *   - Algorithm 1 (the per-pair loop over traces and window samples): the window runs
+ *     along the trace around its own intersection k, reading samples k+j and k+j+1
+ *     with one shared interpolation fraction x for all j, and accumulates num[j],
+ *     den and the linear stack accumulator ac.
+ *   - Section 3.2: the best candidate of each t0 is the one with the largest semblance;
+ *     the stacked trace is the stack accumulator at that candidate.
+ *   - Section 2.2 / Section 3.5: CRS takes the traces of every CDP whose midpoint lies
+ *     within the aperture radius of the central CDP and replaces the NMO hyperbola by
+ *     the (hyperbolic, A/B/C-parameterised) CRS traveltime surface.
+ *
+ * Readings where the paper is silent (each is also listed in the design notes):
+ *   - window: hw = floor(w/2), j = -hw..hw (w odd, so exactly w samples);
+ *   - a trace takes part for a (t0, candidate) only if every sample k-hw .. k+hw+1 lies
+ *     inside the trace and the traveltime is real (and, for CRS, t0 + A*dm >= 0);
+ *     N counts the traces that take part; S = 0 when N == 0 or the energy is 0;
+ *   - argmax ties go to the lowest candidate index;
+ *   - stack = ac / (N * w) at the picked candidate (0 when N == 0);
+ *   - CMP traveltime t = sqrt(t0^2 + C h^2) with C = 4/v^2 and h the half-offset;
+ *   - CRS traveltime t = sqrt((t0 + A dm)^2 + B dm^2 + C h^2), dm = midpoint minus the
+ *     central midpoint (the 2-D hyperbolic CRS operator in A, B, C);
+ *   - gradient (not in the paper): chain rule through the traveltime and the linear
+ *     interpolation with k and the participation mask held fixed;
+ *   - refinement (not in the paper): projected normalised-gradient ascent, see
+ *     seis_oracle_crs_refine.
+ *
+ * All input arrays are the same FP32 arrays the CUDA path receives; every arithmetic
+ * step here is carried out in FP64.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_MAXW 255
+
+/* ------------------------------------------------------------------------- */
+/* Candidate grid, Section 3.2: "the NMO velocity array is generated according to the
+ * upper and lower bounds".  Reading: nc velocities linearly spaced, bounds included,
+ * converted to C = 4/v^2 (the hyperbola t^2 = t0^2 + 4 h^2 / v^2 in half-offset h). */
+void seis_oracle_velocity_grid(double vmin, double vmax, int32_t nc, double* C_out)
+{
+    for (int32_t c = 0; c < nc; ++c) {
+        double v = (nc == 1) ? vmin : vmin + (vmax - vmin) * (double)c / (double)(nc - 1);
+        C_out[c] = 4.0 / (v * v);
+    }
+}
+
+/* Linear grid lo..hi with n points, both ends included (CRS parameter axes). */
+void seis_oracle_linear_grid(double lo, double hi, int32_t n, double* out)
+{
+    for (int32_t i = 0; i < n; ++i)
+        out[i] = (n == 1) ? lo : lo + (hi - lo) * (double)i / (double)(n - 1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Does a trace of ns samples take part when intersected at fractional sample u?
+ * (Algorithm 1 reads samples k+j and k+j+1 for j = -hw..hw, k = floor(u).) */
+static int window_inside(double u, int64_t ns, int hw)
+{
+    if (!(u == u)) return 0;                 /* NaN */
+    double kf = floor(u);
+    return (kf - hw >= 0.0) && (kf + hw + 1.0 <= (double)(ns - 1));
+}
+
+/* One intersection, Algorithm 1 inner loop: interpolate v = (c[j+1]-c[j])*x + c[j]
+ * along the window and accumulate the semblance numerator terms, the energy and the
+ * linear stack.  Returns 1 if the trace took part. */
+static int intersect(const float* f, int64_t ns, double u, int hw,
+                     double* num, double* den, double* ac)
+{
+    if (!window_inside(u, ns, hw)) return 0;
+    double kf = floor(u);
+    int64_t k = (int64_t)kf;
+    double x = u - kf;
+    for (int j = -hw; j <= hw; ++j) {
+        double c0 = (double)f[k + j];
+        double c1 = (double)f[k + j + 1];
+        double v = (c1 - c0) * x + c0;
+        num[j + hw] += v;
+        *den += v * v;
+        *ac += v;
+    }
+    return 1;
+}
+
+/* Eq. 1 with the 1/N normalisation; 0 for an empty or energy-free window. */
+static double semblance_of(const double* num, int w, double den, int64_t N)
+{
+    if (N == 0 || !(den > 0.0)) return 0.0;
+    double nu = 0.0;
+    for (int j = 0; j < w; ++j) nu += num[j] * num[j];
+    return nu / ((double)N * den);
+}
+
+/* Parity bookkeeping for FP32 implementations: a (row, candidate) is flagged when some
+ * trace's participation would change if u moved by +-eps samples (a mask edge sitting
+ * on an interpolation knot); see the design notes' reading c5. */
+static int edge_sensitive(double u, int64_t ns, int hw, double eps)
+{
+    return window_inside(u - eps, ns, hw) != window_inside(u + eps, ns, hw);
+}
+
+/* Output row r -> (owner index, local sample n) by binary search in off[0..cnt]. */
+static int64_t owner_of(const int64_t* off, int64_t cnt, int64_t r)
+{
+    int64_t lo = 0, hi = cnt - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if (off[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+static void set_threads(int32_t nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* CMP semblance search (Section 2.1, Eq. 1, Algorithm 1, Section 3.2).
+ *
+ * traces      [trace_off[ntr]] FP32 samples; trace i = traces[trace_off[i] .. trace_off[i+1])
+ * h           [ntr] half-offset of each trace (m)
+ * gather_off  [G+1] trace range of each CMP gather
+ * out_off     [G+1] output rows of each gather: gather g has out_off[g+1]-out_off[g]
+ *             output samples t0 = n*dt[g]
+ * dt          [G] sampling interval of each gather (s)
+ * C           [nc] candidate C = 4/v^2 values (s^2/m^2)
+ * rows        global output rows to evaluate (NULL: all rows 0..out_off[G]-1)
+ * Outputs are per evaluated row (index e = 0..nrows-1); any may be NULL:
+ *   S[e*nc+c], Nvalid[e*nc+c], edge[e*nc+c], best_idx[e], best_S[e], second_S[e]
+ *   (largest S among the other candidates), stack[e].
+ * Returns 0, or -1 on invalid arguments. */
+int seis_oracle_cmp(const float* traces, const int64_t* trace_off, const float* h,
+                    const int64_t* gather_off, const int64_t* out_off, const float* dt,
+                    int64_t G, const float* C, int32_t nc, int32_t w,
+                    const int64_t* rows, int64_t nrows,
+                    double* S, int32_t* Nvalid, int8_t* edge,
+                    int32_t* best_idx, double* best_S, double* second_S, double* stack,
+                    double knot_eps, int32_t nthreads)
+{
+    if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || nc < 1 || G < 1) return -1;
+    const int hw = w / 2;
+    const int64_t total_rows = out_off[G];
+    if (!rows) nrows = total_rows;
+    set_threads(nthreads);
+
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t e = 0; e < nrows; ++e) {
+        const int64_t r = rows ? rows[e] : e;
+        const int64_t g = owner_of(out_off, G, r);
+        const int64_t n = r - out_off[g];
+        const double dtg = (double)dt[g];
+        const double t0 = (double)n * dtg;
+        double num[ORACLE_MAXW];
+        int32_t bi = -1; double bs = -1.0, b2 = -1.0, bst = 0.0;
+        for (int32_t c = 0; c < nc; ++c) {
+            const double Cc = (double)C[c];
+            double den = 0.0, ac = 0.0; int64_t N = 0; int flag = 0;
+            memset(num, 0, sizeof(double) * (size_t)w);
+            for (int64_t i = gather_off[g]; i < gather_off[g + 1]; ++i) {
+                const double hi = (double)h[i];
+                const int64_t ns_i = trace_off[i + 1] - trace_off[i];
+                const double rad = t0 * t0 + Cc * hi * hi;            /* t^2, Section 2.1 */
+                if (!(rad >= 0.0)) continue;
+                const double u = sqrt(rad) / dtg;                      /* traveltime in samples */
+                if (edge && edge_sensitive(u, ns_i, hw, knot_eps)) flag = 1;
+                N += intersect(traces + trace_off[i], ns_i, u, hw, num, &den, &ac);
+            }
+            const double s = semblance_of(num, w, den, N);
+            if (S) S[e * nc + c] = s;
+            if (Nvalid) Nvalid[e * nc + c] = (int32_t)N;
+            if (edge) edge[e * nc + c] = (int8_t)flag;
+            if (s > bs) { b2 = bs; bs = s; bi = c; bst = N ? ac / ((double)N * w) : 0.0; }
+            else if (s > b2) b2 = s;
+        }
+        if (best_idx) best_idx[e] = bi;
+        if (best_S) best_S[e] = bs;
+        if (second_S) second_S[e] = b2;
+        if (stack) stack[e] = bst;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* CRS aperture (Section 2.2, Section 3.5): for each central gather, every trace whose
+ * midpoint lies within the radius apm of the central CDP's midpoint (inclusive).  The
+ * central midpoint is the midpoint of the central gather's first trace.  Traces are
+ * listed in increasing trace index.  nbr_off has n_central+1 entries; nbr_trace may be
+ * NULL to count only.  m_c receives the central midpoints (may be NULL). */
+int seis_oracle_neighbours(const float* m, const int64_t* gather_off, int64_t G,
+                           const int32_t* central, int64_t n_central, double apm,
+                           int64_t* nbr_off, int32_t* nbr_trace, float* m_c)
+{
+    const int64_t ntr = gather_off[G];
+    nbr_off[0] = 0;
+    for (int64_t c = 0; c < n_central; ++c) {
+        const int32_t g = central[c];
+        if (g < 0 || g >= G || gather_off[g + 1] <= gather_off[g]) return -1;
+        const double mg = (double)m[gather_off[g]];
+        if (m_c) m_c[c] = m[gather_off[g]];
+        int64_t cnt = 0;
+        for (int64_t i = 0; i < ntr; ++i) {
+            if (fabs((double)m[i] - mg) <= apm) {
+                if (nbr_trace) nbr_trace[nbr_off[c] + cnt] = (int32_t)i;
+                ++cnt;
+            }
+        }
+        nbr_off[c + 1] = nbr_off[c] + cnt;
+    }
+    return 0;
+}
+
+/* CRS traveltime in samples for one trace (reading c11):
+ *   t^2 = (t0 + A dm)^2 + B dm^2 + C h^2; returns 0 when the trace cannot take part
+ *   (t0 + A dm < 0 or t^2 < 0).  p_out, t_out receive t0 + A dm and t (s). */
+static int crs_time(double t0, double A, double B, double Cc, double dm, double hh,
+                    double dtg, double* u_out, double* p_out, double* t_out)
+{
+    const double p = t0 + A * dm;
+    const double rad = p * p + B * dm * dm + Cc * hh * hh;
+    if (!(p >= 0.0) || !(rad >= 0.0)) return 0;
+    const double t = sqrt(rad);
+    *u_out = t / dtg;
+    if (p_out) *p_out = p;
+    if (t_out) *t_out = t;
+    return 1;
+}
+
+/* CRS semblance search over the flattened A x B x C grid, cand = (ia*nB + ib)*nC + ic.
+ * Central c uses traces nbr_trace[nbr_off[c] .. nbr_off[c+1]) with dm = m[i] - m_c[c],
+ * has out_off_c[c+1]-out_off_c[c] output samples at interval dt_c[c].
+ * Outputs as seis_oracle_cmp (S, Nvalid, edge are [nrows][nA*nB*nC]). */
+int seis_oracle_crs(const float* traces, const int64_t* trace_off, const float* h,
+                    const float* m, const int64_t* nbr_off, const int32_t* nbr_trace,
+                    const float* m_c, const int64_t* out_off_c, const float* dt_c,
+                    int64_t n_central,
+                    const float* A, int32_t nA, const float* B, int32_t nB,
+                    const float* C, int32_t nC, int32_t w,
+                    const int64_t* rows, int64_t nrows,
+                    double* S, int32_t* Nvalid, int8_t* edge,
+                    int32_t* best_idx, double* best_S, double* second_S, double* stack,
+                    double knot_eps, int32_t nthreads)
+{
+    if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || nA < 1 || nB < 1 || nC < 1 || n_central < 1)
+        return -1;
+    const int hw = w / 2;
+    const int64_t ncand = (int64_t)nA * nB * nC;
+    const int64_t total_rows = out_off_c[n_central];
+    if (!rows) nrows = total_rows;
+    set_threads(nthreads);
+
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t e = 0; e < nrows; ++e) {
+        const int64_t r = rows ? rows[e] : e;
+        const int64_t c = owner_of(out_off_c, n_central, r);
+        const int64_t n = r - out_off_c[c];
+        const double dtg = (double)dt_c[c];
+        const double t0 = (double)n * dtg;
+        const double mc = (double)m_c[c];
+        double num[ORACLE_MAXW];
+        int32_t bi = -1; double bs = -1.0, b2 = -1.0, bst = 0.0;
+        for (int64_t cand = 0; cand < ncand; ++cand) {
+            const int64_t ia = cand / ((int64_t)nB * nC);
+            const int64_t ib = (cand / nC) % nB;
+            const int64_t ic = cand % nC;
+            const double Av = (double)A[ia], Bv = (double)B[ib], Cv = (double)C[ic];
+            double den = 0.0, ac = 0.0; int64_t N = 0; int flag = 0;
+            memset(num, 0, sizeof(double) * (size_t)w);
+            for (int64_t q = nbr_off[c]; q < nbr_off[c + 1]; ++q) {
+                const int64_t i = nbr_trace[q];
+                const double dm = (double)m[i] - mc;
+                const int64_t ns_i = trace_off[i + 1] - trace_off[i];
+                double u, p;
+                const double rad = (t0 + Av * dm) * (t0 + Av * dm) + Bv * dm * dm
+                                   + Cv * (double)h[i] * (double)h[i];
+                if (edge) {
+                    /* participation flips for a tiny change of p or t^2, or of u */
+                    if (fabs(t0 + Av * dm) < knot_eps * dtg || fabs(rad) < knot_eps * dtg * dtg)
+                        flag = 1;
+                }
+                if (!crs_time(t0, Av, Bv, Cv, dm, (double)h[i], dtg, &u, &p, NULL)) continue;
+                if (edge && edge_sensitive(u, ns_i, hw, knot_eps)) flag = 1;
+                N += intersect(traces + trace_off[i], ns_i, u, hw, num, &den, &ac);
+            }
+            const double s = semblance_of(num, w, den, N);
+            if (S) S[e * ncand + cand] = s;
+            if (Nvalid) Nvalid[e * ncand + cand] = (int32_t)N;
+            if (edge) edge[e * ncand + cand] = (int8_t)flag;
+            if (s > bs) { b2 = bs; bs = s; bi = (int32_t)cand; bst = N ? ac / ((double)N * w) : 0.0; }
+            else if (s > b2) b2 = s;
+        }
+        if (best_idx) best_idx[e] = bi;
+        if (best_S) best_S[e] = bs;
+        if (second_S) second_S[e] = b2;
+        if (stack) stack[e] = bst;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Semblance, stack and analytic gradient of one CRS operator per output row (readings
+ * c8 and c15).  theta[e*3 + {0,1,2}] = (A, B, C) for evaluated row e.  CMP is the case
+ * A = B = 0 with the gather's own traces as the neighbour list.
+ *
+ * Gradient, with k and the participation mask held fixed (derivative almost everywhere):
+ *   du/dA = (t0 + A dm) dm / (t dt),  du/dB = dm^2 / (2 t dt),  du/dC = h^2 / (2 t dt)
+ *   dv_j/dtheta = (f[k+j+1] - f[k+j]) du/dtheta
+ *   dS/dtheta = (dNu * N den - Nu * N dden) / (N den)^2,  Nu = sum_j num_j^2. */
+static void crs_eval_one(const float* traces, const int64_t* trace_off, const float* h,
+                         const float* m, const int32_t* list, int64_t cnt, double mc,
+                         double t0, double dtg, int hw, const double* th,
+                         double* S_out, double* grad_out, double* stack_out, int32_t* N_out)
+{
+    const int w = 2 * hw + 1;
+    double num[ORACLE_MAXW], dnum[3][ORACLE_MAXW];
+    double den = 0.0, ac = 0.0, dden[3] = {0.0, 0.0, 0.0};
+    int64_t N = 0;
+    memset(num, 0, sizeof(num));
+    memset(dnum, 0, sizeof(dnum));
+    for (int64_t q = 0; q < cnt; ++q) {
+        const int64_t i = list[q];
+        const double dm = (double)m[i] - mc;
+        const double hh = (double)h[i];
+        const int64_t ns_i = trace_off[i + 1] - trace_off[i];
+        double u, p, t;
+        if (!crs_time(t0, th[0], th[1], th[2], dm, hh, dtg, &u, &p, &t)) continue;
+        if (!window_inside(u, ns_i, hw)) continue;
+        const float* f = traces + trace_off[i];
+        const double kf = floor(u);
+        const int64_t k = (int64_t)kf;
+        const double x = u - kf;
+        double du[3] = {0.0, 0.0, 0.0};
+        if (t > 0.0) {
+            du[0] = p * dm / (t * dtg);
+            du[1] = dm * dm / (2.0 * t * dtg);
+            du[2] = hh * hh / (2.0 * t * dtg);
+        }
+        for (int j = -hw; j <= hw; ++j) {
+            const double c0 = (double)f[k + j], c1 = (double)f[k + j + 1];
+            const double d = c1 - c0;
+            const double v = d * x + c0;
+            num[j + hw] += v;
+            den += v * v;
+            ac += v;
+            for (int a = 0; a < 3; ++a) {
+                dnum[a][j + hw] += d * du[a];
+                dden[a] += 2.0 * v * d * du[a];
+            }
+        }
+        ++N;
+    }
+    double nu = 0.0, dnu[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < w; ++j) {
+        nu += num[j] * num[j];
+        for (int a = 0; a < 3; ++a) dnu[a] += 2.0 * num[j] * dnum[a][j];
+    }
+    if (N == 0 || !(den > 0.0)) {
+        *S_out = 0.0;
+        if (grad_out) grad_out[0] = grad_out[1] = grad_out[2] = 0.0;
+    } else {
+        const double D = (double)N * den;
+        *S_out = nu / D;
+        if (grad_out)
+            for (int a = 0; a < 3; ++a)
+                grad_out[a] = (dnu[a] * D - nu * (double)N * dden[a]) / (D * D);
+    }
+    if (stack_out) *stack_out = N ? ac / ((double)N * w) : 0.0;
+    if (N_out) *N_out = (int32_t)N;
+}
+
+/* Evaluate S, dS/d(A,B,C) and the stack at given operators, one per row. */
+int seis_oracle_crs_eval(const float* traces, const int64_t* trace_off, const float* h,
+                         const float* m, const int64_t* nbr_off, const int32_t* nbr_trace,
+                         const float* m_c, const int64_t* out_off_c, const float* dt_c,
+                         int64_t n_central, int32_t w,
+                         const int64_t* rows, int64_t nrows, const double* theta,
+                         double* S, double* grad, double* stack, int32_t* Nvalid,
+                         int32_t nthreads)
+{
+    if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || n_central < 1) return -1;
+    const int hw = w / 2;
+    if (!rows) nrows = out_off_c[n_central];
+    set_threads(nthreads);
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t e = 0; e < nrows; ++e) {
+        const int64_t r = rows ? rows[e] : e;
+        const int64_t c = owner_of(out_off_c, n_central, r);
+        const int64_t n = r - out_off_c[c];
+        const double dtg = (double)dt_c[c];
+        double s, st; int32_t N;
+        crs_eval_one(traces, trace_off, h, m, nbr_trace + nbr_off[c], nbr_off[c + 1] - nbr_off[c],
+                     (double)m_c[c], (double)n * dtg, dtg, hw, theta + 3 * e,
+                     &s, grad ? grad + 3 * e : NULL, &st, &N);
+        if (S) S[e] = s;
+        if (stack) stack[e] = st;
+        if (Nvalid) Nvalid[e] = N;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gradient-ascent refinement of the CRS operator from a coarse pick (reading c16).
+ * Per row, in normalised coordinates z = (theta - lo) / (hi - lo):
+ *   start at z0 (theta_in), step s = step0; evaluate S(z), g = dS/dz;
+ *   repeat `steps` times: if |g| == 0 stop; trial z' = clamp(z + s g/|g|, 0, 1);
+ *     evaluate S(z'); if S(z') >= S(z) accept (z, S, g) <- (z', S', g'), else s <- s/2.
+ * Outputs theta_out [nrows*3], S_out, grad_out (dS/dtheta at the final point, may be
+ * NULL), stack_out (may be NULL). */
+int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const float* h,
+                           const float* m, const int64_t* nbr_off, const int32_t* nbr_trace,
+                           const float* m_c, const int64_t* out_off_c, const float* dt_c,
+                           int64_t n_central, int32_t w,
+                           const int64_t* rows, int64_t nrows, const double* theta_in,
+                           const double* lo3, const double* hi3, int32_t steps, double step0,
+                           double* theta_out, double* S_out, double* grad_out, double* stack_out,
+                           int32_t nthreads)
+{
+    if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || n_central < 1 || steps < 0) return -1;
+    for (int a = 0; a < 3; ++a) if (!(hi3[a] > lo3[a])) return -1;
+    const int hw = w / 2;
+    if (!rows) nrows = out_off_c[n_central];
+    set_threads(nthreads);
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t e = 0; e < nrows; ++e) {
+        const int64_t r = rows ? rows[e] : e;
+        const int64_t c = owner_of(out_off_c, n_central, r);
+        const int64_t n = r - out_off_c[c];
+        const double dtg = (double)dt_c[c];
+        const int32_t* list = nbr_trace + nbr_off[c];
+        const int64_t cnt = nbr_off[c + 1] - nbr_off[c];
+        const double t0 = (double)n * dtg, mc = (double)m_c[c];
+        double z[3], th[3], g[3], gz[3], s, st;
+        for (int a = 0; a < 3; ++a) {
+            z[a] = (theta_in[3 * e + a] - lo3[a]) / (hi3[a] - lo3[a]);
+            th[a] = theta_in[3 * e + a];
+        }
+        crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th, &s, g, &st, NULL);
+        double step = step0;
+        for (int it = 0; it < steps; ++it) {
+            double gn = 0.0;
+            for (int a = 0; a < 3; ++a) { gz[a] = g[a] * (hi3[a] - lo3[a]); gn += gz[a] * gz[a]; }
+            gn = sqrt(gn);
+            if (!(gn > 0.0)) break;
+            double z2[3], th2[3], g2[3], s2, st2;
+            for (int a = 0; a < 3; ++a) {
+                double zz = z[a] + step * gz[a] / gn;
+                z2[a] = zz < 0.0 ? 0.0 : (zz > 1.0 ? 1.0 : zz);
+                th2[a] = lo3[a] + z2[a] * (hi3[a] - lo3[a]);
+            }
+            crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th2, &s2, g2, &st2, NULL);
+            if (s2 >= s) {
+                for (int a = 0; a < 3; ++a) { z[a] = z2[a]; th[a] = th2[a]; g[a] = g2[a]; }
+                s = s2; st = st2;
+            } else {
+                step *= 0.5;
+            }
+        }
+        for (int a = 0; a < 3; ++a) theta_out[3 * e + a] = th[a];
+        if (S_out) S_out[e] = s;
+        if (grad_out) for (int a = 0; a < 3; ++a) grad_out[3 * e + a] = g[a];
+        if (stack_out) stack_out[e] = st;
+    }
+    return 0;
+}
+
+int seis_oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

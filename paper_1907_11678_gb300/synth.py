@@ -1,0 +1,214 @@
+"""Seeded synthetic seismic gathers shaped like the paper's workloads.
+
+The paper's datasets (Table 1) are synthetic and unpublished, so every input here is
+generated: Ricker-wavelet reflection events on CMP gathers with Gaussian noise at a
+given signal-to-noise ratio.  This module does forward modelling only (event
+traveltimes and wavelets); it contains none of the semblance search's arithmetic
+(no interpolation, semblance, pick or stack), and it is the one module that feeds
+both the CUDA path and the FP64 oracle.
+
+Event traveltimes (two-way, half-offset h, midpoint m, all in SI units):
+  * hyperbolic event on one CMP:      t = sqrt(t0^2 + 4 h^2 / v^2)
+  * dipping plane, constant velocity: t = sqrt((t0c + 2 sin(a) (m - mc) / v)^2 + 4 cos(a)^2 h^2 / v^2)
+  * point diffractor at (xd, zd):     t = (sqrt(zd^2 + (m - h - xd)^2) + sqrt(zd^2 + (m + h - xd)^2)) / v
+Wavelet: Ricker r(tau) = (1 - 2 pi^2 f^2 tau^2) exp(-pi^2 f^2 tau^2), f = 25 Hz.
+Noise: sigma_g = RMS of gather g's noise-free samples with |s| > 1e-3 * peak, divided by
+SNR; seeded numpy PCG64 streams per block of gathers.
+
+A dataset is a dict of numpy arrays:
+  traces     float32 [total_samples]  trace i = traces[trace_off[i]:trace_off[i+1]]
+  trace_off  int64   [ntraces+1]
+  h          float32 [ntraces]        half-offset (m)
+  m          float32 [ntraces]        midpoint of the trace's CDP (m)
+  gather_off int64   [G+1]            traces of gather g
+  out_off    int64   [G+1]            output rows of gather g (its number of samples)
+  dt         float32 [G]              sampling interval (s)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+RICKER_HZ = 25.0
+_BLOCK = 64  # gathers per noise stream
+
+
+def ricker(tau, f=RICKER_HZ):
+    a = (np.pi * f * tau) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def _layout(ns_per_trace, traces_per_gather, out_ns):
+    ns_per_trace = np.asarray(ns_per_trace, np.int64)
+    trace_off = np.zeros(len(ns_per_trace) + 1, np.int64)
+    np.cumsum(ns_per_trace, out=trace_off[1:])
+    gather_off = np.zeros(len(traces_per_gather) + 1, np.int64)
+    np.cumsum(np.asarray(traces_per_gather, np.int64), out=gather_off[1:])
+    out_off = np.zeros(len(out_ns) + 1, np.int64)
+    np.cumsum(np.asarray(out_ns, np.int64), out=out_off[1:])
+    return trace_off, gather_off, out_off
+
+
+def _add_events_uniform(block, times, amps, dt, f=RICKER_HZ):
+    """block: float64 [R, ns]; times: [E, R] traveltimes (s, NaN = absent); amps [E, R]."""
+    R, ns = block.shape
+    half = int(np.ceil(1.5 / (f * dt))) + 1  # Ricker is below 1e-9 beyond |tau| = 1.5/f
+    rows = np.arange(R)
+    for e in range(times.shape[0]):
+        t = times[e]
+        ok = np.isfinite(t)
+        centre = np.where(ok, np.floor(np.where(ok, t, 0.0) / dt), -10 * half).astype(np.int64)
+        for o in range(-half, half + 2):
+            s = centre + o
+            sel = ok & (s >= 0) & (s < ns)
+            if not sel.any():
+                continue
+            r, ss = rows[sel], s[sel]
+            block[r, ss] += amps[e, sel] * ricker(ss * dt - t[sel], f)
+
+
+def _noise_sigma(block_g, snr):
+    """block_g: [G, M*ns] noise-free samples; per-gather sigma."""
+    peak = np.abs(block_g).max(axis=1)
+    sig = np.zeros(block_g.shape[0])
+    for g in range(block_g.shape[0]):
+        if peak[g] <= 0:
+            continue
+        sel = np.abs(block_g[g]) > 1e-3 * peak[g]
+        sig[g] = np.sqrt(np.mean(block_g[g][sel] ** 2)) / snr
+    if (sig == 0).any() and (sig > 0).any():
+        sig[sig == 0] = np.median(sig[sig > 0])
+    return sig
+
+
+def _finish(traces64, snr, seed, G, per_gather_len, blk0=0):
+    """Add seeded noise gather-block-wise and return float32."""
+    out = np.empty(traces64.size, np.float32)
+    L = per_gather_len
+    for b0 in range(0, G, _BLOCK):
+        b1 = min(G, b0 + _BLOCK)
+        blk = traces64[b0 * L:b1 * L].reshape(b1 - b0, L)
+        if snr is not None and snr > 0:
+            sig = _noise_sigma(blk, snr)
+            rng = np.random.default_rng([seed, blk0 + b0 // _BLOCK])
+            noise = rng.standard_normal((b1 - b0, L))
+            blk = blk + noise * sig[:, None]
+        out[b0 * L:b1 * L] = blk.reshape(-1)
+    return out
+
+
+def cmp_line(G, M, ns, dt, hmin, hmax, n_events, snr, seed, t0_range=None,
+             v_range=(1500.0, 4000.0), v_gradient=0.0, dm=12.5, amp_range=(0.5, 1.0)):
+    """G CMP gathers on a line (spacing dm), M traces with half-offsets evenly spaced in
+    [hmin, hmax], ns samples at dt.  n_events hyperbolic events per gather with t0 ~
+    U(t0_range), amplitude +-U(amp_range) and velocity v0 + v_gradient*(g - G/2), v0 ~
+    U(v_range) (shared along the line)."""
+    rng = np.random.default_rng(seed)
+    T = ns * dt
+    if t0_range is None:
+        t0_range = (0.3, 0.9 * T)
+    t0 = rng.uniform(*t0_range, size=n_events)
+    v0 = rng.uniform(*v_range, size=n_events)
+    amp = rng.uniform(*amp_range, size=n_events) * rng.choice([-1.0, 1.0], size=n_events)
+    h = np.linspace(hmin, hmax, M)
+    g = np.arange(G)
+    vel = v0[:, None] + v_gradient * (g[None, :] - G / 2.0)           # [E, G]
+    tt = np.sqrt(t0[:, None, None] ** 2 + 4.0 * h[None, None, :] ** 2 / vel[:, :, None] ** 2)
+    times = tt.reshape(n_events, G * M)
+    amps = np.repeat(amp[:, None], G * M, axis=1)
+    block = np.zeros((G * M, ns))
+    _add_events_uniform(block, times, amps, dt)
+    traces = _finish(block.reshape(-1), snr, seed, G, M * ns)
+    trace_off, gather_off, out_off = _layout(np.full(G * M, ns), np.full(G, M), np.full(G, ns))
+    return dict(traces=traces, trace_off=trace_off,
+                h=np.tile(h, G).astype(np.float32),
+                m=np.repeat(g * dm, M).astype(np.float32),
+                gather_off=gather_off, out_off=out_off,
+                dt=np.full(G, dt, np.float32),
+                events=dict(t0=t0, v0=v0, amp=amp, v_gradient=v_gradient))
+
+
+def crs_line(G, M, ns, dt, hmin, hmax, n_planes, n_diffractors, snr, seed, dm=12.5,
+             v_range=(1500.0, 4000.0), max_dip_deg=20.0, amp_range=(0.5, 1.0)):
+    """A 2-D line of G CMPs (spacing dm) with dipping planar reflectors (exact CRS form,
+    B = 0) and point diffractors (double-square-root traveltime)."""
+    rng = np.random.default_rng(seed)
+    T = ns * dt
+    mid = np.arange(G) * dm
+    mcen = mid[G // 2]
+    h = np.linspace(hmin, hmax, M)
+    Mm = np.repeat(mid, M)
+    Hh = np.tile(h, G)
+    times, amps, planes, diffs = [], [], [], []
+    for _ in range(n_planes):
+        t0c = rng.uniform(0.3, 0.85 * T)
+        v = rng.uniform(*v_range)
+        a = np.deg2rad(rng.uniform(-max_dip_deg, max_dip_deg))
+        amp = rng.uniform(*amp_range) * rng.choice([-1.0, 1.0])
+        t0m = t0c + 2.0 * np.sin(a) * (Mm - mcen) / v
+        t = np.where(t0m > 0, np.sqrt(np.maximum(t0m, 0) ** 2 + 4.0 * np.cos(a) ** 2 * Hh ** 2 / v ** 2),
+                     np.nan)
+        times.append(t); amps.append(np.full(G * M, amp))
+        planes.append(dict(t0c=t0c, v=v, dip=a, amp=amp, mc=mcen))
+    for _ in range(n_diffractors):
+        v = rng.uniform(*v_range)
+        xd = rng.uniform(mid[0], mid[-1])
+        zd = rng.uniform(0.3, 0.8 * T) * v / 2.0
+        amp = rng.uniform(*amp_range) * rng.choice([-1.0, 1.0])
+        t = (np.sqrt(zd ** 2 + (Mm - Hh - xd) ** 2) + np.sqrt(zd ** 2 + (Mm + Hh - xd) ** 2)) / v
+        times.append(t); amps.append(np.full(G * M, amp))
+        diffs.append(dict(xd=xd, zd=zd, v=v, amp=amp))
+    block = np.zeros((G * M, ns))
+    if times:
+        _add_events_uniform(block, np.array(times), np.array(amps), dt)
+    traces = _finish(block.reshape(-1), snr, seed, G, M * ns)
+    trace_off, gather_off, out_off = _layout(np.full(G * M, ns), np.full(G, M), np.full(G, ns))
+    return dict(traces=traces, trace_off=trace_off, h=Hh.astype(np.float32),
+                m=Mm.astype(np.float32), gather_off=gather_off, out_off=out_off,
+                dt=np.full(G, dt, np.float32), events=dict(planes=planes, diffractors=diffs))
+
+
+# --- the workloads (shapes from the paper's problem statement; see the design notes) --
+
+CMP_V_RANGE = (1400.0, 4500.0)
+
+
+def workload_cmp_small(seed=1):
+    """16 CMP gathers, fold 24, h 0..1500 m, 1000 samples at 4 ms, 5 events, SNR 2."""
+    return cmp_line(16, 24, 1000, 0.004, 0.0, 1500.0, 5, 2.0, seed, t0_range=(0.3, 3.5))
+
+
+def workload_cmp_line(seed=2, G=4096):
+    """4096 CMP gathers on a line, fold 60, h 25..3000 m, 2000 samples at 4 ms, 8 events
+    with a lateral velocity gradient of 0.5 m/s per CMP, SNR 1."""
+    return cmp_line(G, 60, 2000, 0.004, 25.0, 3000.0, 8, 1.0, seed,
+                    v_range=(2550.0, 3450.0), v_gradient=0.5)
+
+
+def workload_crs_line(seed=3, n_central=1024, pad=10):
+    """1024 central CMPs + 10 padding CMPs each side at 12.5 m, fold 48, h 0..2400 m,
+    1500 samples at 4 ms; dipping planes and diffractors, SNR 2."""
+    rng = np.random.default_rng(seed + 1000)
+    ds = crs_line(n_central + 2 * pad, 48, 1500, 0.004, 0.0, 2400.0,
+                  int(rng.integers(3, 5)), int(rng.integers(2, 4)), 2.0, seed)
+    ds["central"] = np.arange(pad, pad + n_central, dtype=np.int32)
+    ds["apm"] = pad * 12.5
+    return ds
+
+
+def workload_crs_refine(seed=5, n_central=512, pad=8):
+    """512 central CMPs, aperture +-8 CMPs (100 m), fold 48, 2000 samples at 4 ms."""
+    rng = np.random.default_rng(seed + 1000)
+    ds = crs_line(n_central + 2 * pad, 48, 2000, 0.004, 0.0, 2400.0,
+                  int(rng.integers(3, 5)), int(rng.integers(2, 4)), 2.0, seed)
+    ds["central"] = np.arange(pad, pad + n_central, dtype=np.int32)
+    ds["apm"] = pad * 12.5
+    return ds
+
+
+def crs_ranges(max_dip_deg=20.0, vmin=1500.0, vlo=1400.0, vhi=4500.0):
+    """(lo, hi) of A, B, C for the CRS grids: A = +-2 sin(dip)/vmin, B = +-4/vlo^2,
+    C = 4/v^2 over [vlo, vhi]."""
+    amax = 2.0 * np.sin(np.deg2rad(max_dip_deg)) / vmin
+    cmax = 4.0 / vlo ** 2
+    cmin = 4.0 / vhi ** 2
+    return (-amax, amax), (-cmax, cmax), (cmin, cmax)

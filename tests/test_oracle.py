@@ -1,0 +1,348 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics, not by
+the oracle itself (CPU only)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_11678_gb300 import synth
+from tests.dsutil import dataset, pythagorean_offsets, spike_wavelet
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --- Eq. 1 worked example (hand-derived, tests/golden) ---------------------------------
+
+def test_worked_example_golden():
+    ex = json.load(open(os.path.join(GOLDEN, "cmp_worked_example.json")))
+    ds = dataset(ex["traces"], ex["h"], ex["dt"])
+    r = oracle.cmp_semblance(ds, np.array(ex["C"]), w=ex["w"], rows=[ex["row"]])
+    np.testing.assert_allclose(r.S[0], ex["expect_S"], rtol=0, atol=1e-15)
+    assert list(r.N[0]) == ex["expect_N"]
+    assert r.best_idx[0] == ex["expect_best_idx"]
+    assert r.stack[0] == pytest.approx(ex["expect_stack"], abs=1e-15)
+    # stack at each candidate: one-candidate searches
+    for c, want in enumerate(ex["expect_stack_per_candidate"]):
+        rc = oracle.cmp_semblance(ds, np.array([ex["C"][c]]), w=ex["w"], rows=[ex["row"]])
+        assert rc.stack[0] == pytest.approx(want, abs=1e-15)
+
+
+# --- Eq. 1 closed forms and invariants ----------------------------------------------------
+
+def _grid(nc=21):
+    return oracle.velocity_grid(1400.0, 4500.0, nc)
+
+
+def test_velocity_grid_closed_form():
+    C = oracle.velocity_grid(1400.0, 4500.0, 5)
+    v = np.array([1400.0, 2175.0, 2950.0, 3725.0, 4500.0])
+    np.testing.assert_allclose(C, 4.0 / v ** 2, rtol=1e-15)
+    assert oracle.velocity_grid(2000.0, 3000.0, 1)[0] == pytest.approx(1e-6)
+
+
+def test_constant_traces_semblance_one():
+    rng = np.random.default_rng(0)
+    M, ns = 12, 300
+    h = np.linspace(0, 1500, M)
+    c0 = rng.uniform(0.5, 2.0)
+    ds = dataset([np.full(ns, c0)] * M, h, 0.004)
+    r = oracle.cmp_semblance(ds, _grid())
+    has = r.N > 0
+    assert has.any() and (~has).any()
+    np.testing.assert_allclose(r.S[has], 1.0, atol=1e-14)
+    assert np.all(r.S[~has] == 0.0)
+    # unequal constants c_i, every trace taking part: S = (sum c)^2 / (N sum c^2)
+    cs = rng.uniform(-1.0, 2.0, M).astype(np.float32).astype(np.float64)
+    ds2 = dataset([np.full(ns, c) for c in cs], h, 0.004)
+    r2 = oracle.cmp_semblance(ds2, _grid())
+    full = r2.N == M
+    assert full.sum() > 100
+    np.testing.assert_allclose(r2.S[full], cs.sum() ** 2 / (M * (cs ** 2).sum()), rtol=1e-12)
+
+
+def test_single_trace_semblance_one():
+    rng = np.random.default_rng(1)
+    ds = dataset([rng.standard_normal(400)], [800.0], 0.004)
+    r = oracle.cmp_semblance(ds, _grid())
+    one = r.N == 1
+    np.testing.assert_allclose(r.S[one], 1.0, atol=1e-13)
+    assert np.all(r.S[r.N == 0] == 0.0)
+
+
+def test_zero_data():
+    ds = dataset([np.zeros(200)] * 5, np.linspace(0, 1000, 5), 0.004)
+    r = oracle.cmp_semblance(ds, _grid())
+    assert np.all(r.S == 0.0) and np.all(r.stack == 0.0)
+
+
+def test_random_bounds_cauchy_schwarz():
+    ds = synth.cmp_line(3, 17, 500, 0.004, 0.0, 2000.0, 3, 0.5, seed=7)
+    r = oracle.cmp_semblance(ds, _grid(31))
+    assert r.S.min() >= 0.0 and r.S.max() <= 1.0 + 1e-12
+    assert np.all(r.best_S >= r.second_S)
+
+
+# --- an exactly sampled hyperbolic event: S = 1 at the true C, argmax = true C ---------
+
+def _exact_hyperbola(n0=240, ns=700, hw=5):
+    dt = 1.0 / 256.0
+    Ct = 2.0 ** -20                       # C h^2 / dt^2 = (4a)^2 for h = 16 a
+    trip = [(0, n0)] + pythagorean_offsets(n0, 150)
+    traces, h = [], []
+    for a, mm in trip:
+        traces.append(spike_wavelet(ns, mm, 2.5))
+        h.append(16.0 * a)
+    return dataset(traces, h, dt), Ct, len(trip)
+
+
+def test_exact_hyperbola_semblance_one():
+    ds, Ct, M = _exact_hyperbola()
+    assert M >= 6
+    grid = Ct * np.array([0.5, 0.8, 0.9, 1.0, 1.1, 1.25, 1.6])
+    r = oracle.cmp_semblance(ds, grid, w=11, rows=[240])
+    assert r.N[0, 3] == M
+    assert r.S[0, 3] == pytest.approx(1.0, abs=1e-14)
+    assert r.best_idx[0] == 3
+    assert r.S[0, [0, 1, 2, 4, 5, 6]].max() < 0.99
+
+
+# --- pure-Python brute force on tiny inputs (independent loop nest) ----------------------
+
+def _brute_cmp(traces, h, dt, C, w, ns_out):
+    hw = w // 2
+    S = np.zeros((ns_out, len(C)))
+    for n in range(ns_out):
+        t0 = n * float(dt)
+        for c, Cc in enumerate(C):
+            Cc = float(Cc)
+            num = [0.0] * w
+            den = 0.0
+            N = 0
+            for f, hh in zip(traces, h):
+                f = [float(a) for a in f]
+                u = (t0 * t0 + Cc * float(hh) * float(hh)) ** 0.5 / float(dt)
+                k = int(np.floor(u))
+                if k - hw < 0 or k + hw + 1 > len(f) - 1:
+                    continue
+                x = u - k
+                for j in range(-hw, hw + 1):
+                    v = (f[k + j + 1] - f[k + j]) * x + f[k + j]
+                    num[j + hw] += v
+                    den += v * v
+                N += 1
+            S[n, c] = sum(a * a for a in num) / (N * den) if N and den > 0 else 0.0
+    return S
+
+
+@pytest.mark.parametrize("w", [1, 3, 5])
+def test_bruteforce_tiny(w):
+    rng = np.random.default_rng(w)
+    traces = [rng.standard_normal(37).astype(np.float32) for _ in range(4)]
+    traces.append(rng.standard_normal(29).astype(np.float32))          # a shorter trace
+    h = np.float32([0.0, 110.0, 260.0, 420.0, 333.0])
+    dt = np.float32(0.004)
+    C = np.float32(oracle.velocity_grid(1400.0, 4500.0, 6))
+    ds = dataset(traces, h, dt)
+    r = oracle.cmp_semblance(ds, C, w=w)
+    ref = _brute_cmp(traces, h, dt, C, w, len(traces[0]))
+    np.testing.assert_allclose(r.S, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_multi_gather_rows_subset_matches_full():
+    ds = synth.cmp_line(4, 9, 300, 0.004, 0.0, 1200.0, 2, 2.0, seed=3)
+    C = _grid(11)
+    full = oracle.cmp_semblance(ds, C)
+    rows = np.array([0, 5, 299, 300, 301, 777, 1199])
+    sub = oracle.cmp_semblance(ds, C, rows=rows)
+    np.testing.assert_array_equal(sub.S, full.S[rows])
+    np.testing.assert_array_equal(sub.best_idx, full.best_idx[rows])
+
+
+# --- stack of a single trace: window mean of numpy.interp --------------------------------
+
+def test_single_trace_stack_is_window_mean():
+    rng = np.random.default_rng(5)
+    ns, dt, hh, w = 300, 0.004, 700.0, 11
+    f = rng.standard_normal(ns).astype(np.float32)
+    ds = dataset([f], [hh], dt)
+    C = _grid(9)
+    r = oracle.cmp_semblance(ds, C, w=w)
+    hw = w // 2
+    for n in range(0, ns, 7):
+        c = r.best_idx[n]
+        u = np.sqrt((n * np.float64(np.float32(dt))) ** 2 + np.float64(np.float32(C[c]))
+                    * np.float64(np.float32(hh)) ** 2) / np.float64(np.float32(dt))
+        k = np.floor(u)
+        if k - hw < 0 or k + hw + 1 > ns - 1:
+            assert r.stack[n] == 0.0
+            continue
+        want = np.interp(u + np.arange(-hw, hw + 1), np.arange(ns), f.astype(np.float64)).mean()
+        assert r.stack[n] == pytest.approx(want, rel=1e-12, abs=1e-14)
+
+
+# --- CRS: reductions to CMP, an exactly sampled dipping plane, the aperture ---------------
+
+def test_crs_with_zero_dm_equals_cmp():
+    ds = synth.cmp_line(3, 10, 400, 0.004, 0.0, 1500.0, 3, 2.0, seed=11)
+    C = np.float32(_grid(7))
+    A = np.float32([-3e-4, 0.0, 2e-4])
+    B = np.float32([-1e-6, 5e-7])
+    nb = oracle.cmp_as_crs(ds)           # each gather is its own aperture: dm = 0
+    cr = oracle.crs_semblance(ds, nb, A, B, C, want_cube=True)
+    cm = oracle.cmp_semblance(ds, C)
+    cube = cr.S.reshape(-1, len(A), len(B), len(C))
+    for ia in range(len(A)):
+        for ib in range(len(B)):
+            np.testing.assert_array_equal(cube[:, ia, ib, :], cm.S)
+
+
+def test_crs_flat_identical_cmps_equals_cmp():
+    one = synth.cmp_line(1, 8, 300, 0.004, 0.0, 1200.0, 2, 2.0, seed=12)
+    K = 5
+    traces = [one["traces"][one["trace_off"][i]:one["trace_off"][i + 1]] for i in range(8)] * K
+    h = np.tile(one["h"], K)
+    m = np.repeat(np.arange(K) * 12.5, 8)
+    ds = dataset(traces, h, 0.004, m=m, gather_sizes=[8] * K)
+    nb = oracle.neighbours(ds, [2], 30.0)
+    assert nb[0][-1] == 40
+    out_off_c = np.array([0, 300], np.int64)
+    C = np.float32(_grid(9))
+    cr = oracle.crs_semblance(ds, (*nb, out_off_c, np.float32([0.004])), [0.0], [0.0], C,
+                              want_cube=True)
+    cm = oracle.cmp_semblance(one, C)
+    np.testing.assert_allclose(cr.S, cm.S, rtol=1e-12, atol=1e-14)
+
+
+def _exact_plane(n0=260, ns=700):
+    """Traces whose CRS traveltime with A = 2^-6, B = 0, C = 2^-20 (dt = 1/256) lands on
+    integer samples: u^2 = (n0 + 4 dm)^2 + (4 a)^2 (a Pythagorean triple per dm)."""
+    dt = 1.0 / 256.0
+    traces, h, m = [], [], []
+    for dm in range(-3, 4):
+        p = n0 + 4 * dm
+        for a, mm in [(0, p)] + pythagorean_offsets(p, 90)[:6]:
+            traces.append(spike_wavelet(ns, mm, 2.5))
+            h.append(16.0 * a)
+            m.append(100.0 + dm)
+    ds = dataset(traces, h, dt, m=m, gather_sizes=[len(traces)])
+    return ds, (2.0 ** -6, 0.0, 2.0 ** -20)
+
+
+def test_crs_exact_dipping_plane():
+    ds, (At, Bt, Ct) = _exact_plane()
+    nb = (np.array([0, len(ds["h"])], np.int64), np.arange(len(ds["h"]), dtype=np.int32),
+          np.float32([100.0]), np.array([0, 700], np.int64), np.float32([1.0 / 256]))
+    A = At * np.array([0.5, 1.0, 1.5]); B = np.array([-2.0 ** -10, 0.0, 2.0 ** -10])
+    C = Ct * np.array([0.8, 1.0, 1.2])
+    r = oracle.crs_semblance(ds, nb, A, B, C, rows=[260], want_cube=True)
+    true = (1 * 3 + 1) * 3 + 1
+    assert r.N[0, true] == len(ds["h"])
+    assert r.S[0, true] == pytest.approx(1.0, abs=1e-14)
+    assert r.best_idx[0] == true
+    assert np.delete(r.S[0], true).max() < 0.999
+
+
+def test_crs_exact_B_term():
+    """u^2 = (n0 + 4 dm)^2 + 4 dm^2 + (4a)^2 with A = 2^-6, B = 2^-14, C = 2^-20, dt = 1/256."""
+    n0, ns, dt = 240, 700, 1.0 / 256.0
+    traces, h, m = [], [], []
+    for dm in range(-20, 21):
+        p = n0 + 4 * dm
+        for a in range(0, 150):
+            mm2 = p * p + 4 * dm * dm + 16 * a * a
+            r = int(round(np.sqrt(mm2)))
+            if r * r == mm2 and r < ns - 10:
+                traces.append(spike_wavelet(ns, r, 2.5)); h.append(16.0 * a); m.append(50.0 + dm)
+    assert len(traces) >= 40 and len(set(m)) >= 20
+    ds = dataset(traces, h, dt, m=m)
+    nb = (np.array([0, len(h)], np.int64), np.arange(len(h), dtype=np.int32), np.float32([50.0]),
+          np.array([0, ns], np.int64), np.float32([dt]))
+    A = np.array([2.0 ** -6]); B = 2.0 ** -14 * np.array([0.0, 0.5, 1.0, 2.0]); C = [2.0 ** -20]
+    r = oracle.crs_semblance(ds, nb, A, B, C, rows=[n0], want_cube=True)
+    assert r.N[0, 2] == len(traces)
+    assert r.S[0, 2] == pytest.approx(1.0, abs=1e-14)
+    assert r.best_idx[0] == 2
+    assert np.delete(r.S[0], 2).max() < 0.999
+
+
+def test_neighbours_bruteforce():
+    ds = synth.crs_line(30, 4, 200, 0.004, 0.0, 500.0, 1, 0, None, seed=2)
+    central = np.array([0, 7, 15, 29], np.int32)
+    off, tr, mc = oracle.neighbours(ds, central, 37.5)
+    for c, g in enumerate(central):
+        mg = ds["m"][ds["gather_off"][g]]
+        want = np.nonzero(np.abs(ds["m"].astype(np.float64) - mg) <= 37.5)[0]
+        np.testing.assert_array_equal(tr[off[c]:off[c + 1]], want)
+        assert mc[c] == mg
+    assert off[2] - off[1] == 7 * 4          # interior: +-3 CMPs
+
+
+# --- gradient: central finite differences -------------------------------------------------
+
+def test_gradient_matches_finite_differences():
+    ds = synth.crs_line(9, 12, 600, 0.004, 0.0, 1500.0, 2, 1, 4.0, seed=21)
+    nb = oracle.neighbours(ds, [4], 50.0)
+    nbf = (*nb, np.array([0, 600], np.int64), np.float32([0.004]))
+    (alo, ahi), (blo, bhi), (clo, chi) = synth.crs_ranges()
+    rng = np.random.default_rng(0)
+    rows = np.arange(150, 560, 37)
+    theta = np.stack([rng.uniform(alo, ahi, len(rows)) * 0.5,
+                      rng.uniform(blo, bhi, len(rows)) * 0.5,
+                      rng.uniform(clo, chi * 0.5, len(rows))], axis=1)
+    base = oracle.crs_eval(ds, nbf, theta, rows=rows)
+    scale = np.array([ahi - alo, bhi - blo, chi - clo])
+    checked = 0
+    for a in range(3):
+        fd = {}
+        for hrel in (1e-6, 2.5e-7):
+            hstep = hrel * scale[a]
+            tp = theta.copy(); tp[:, a] += hstep
+            tm = theta.copy(); tm[:, a] -= hstep
+            fd[hrel] = (oracle.crs_eval(ds, nbf, tp, rows=rows).S
+                        - oracle.crs_eval(ds, nbf, tm, rows=rows).S) / (2 * hstep)
+        smooth = np.abs(fd[1e-6] - fd[2.5e-7]) <= 1e-7 * (np.abs(fd[1e-6]) + 1e-3 / scale[a])
+        g = base.grad[:, a]
+        err = np.abs(g - fd[1e-6]) / (np.abs(fd[1e-6]) + 1e-3 / scale[a])
+        assert np.all(err[smooth] < 1e-6), (a, err[smooth].max())
+        checked += smooth.sum()
+    assert checked >= 20
+
+
+def test_eval_matches_search_at_grid_point():
+    ds = synth.crs_line(7, 10, 500, 0.004, 0.0, 1500.0, 2, 1, 2.0, seed=31)
+    nb = oracle.neighbours(ds, [3], 40.0)
+    nbf = (*nb, np.array([0, 500], np.int64), np.float32([0.004]))
+    A = np.float32([-2e-4, 0.0, 3e-4]); B = np.float32([0.0, 1e-6]); C = np.float32(_grid(5))
+    rows = np.arange(100, 480, 41)
+    s = oracle.crs_semblance(ds, nbf, A, B, C, rows=rows, want_cube=True)
+    ia, ib, ic = 2, 1, 3
+    th = np.tile(np.float64([A[ia], B[ib], C[ic]]), (len(rows), 1))
+    e = oracle.crs_eval(ds, nbf, th, rows=rows)
+    np.testing.assert_allclose(e.S, s.S[:, (ia * 2 + ib) * 5 + ic], rtol=1e-13, atol=1e-15)
+
+
+# --- refinement invariants (reading c16; beyond these the result is unpinned) ------------
+
+def test_refine_invariants_and_exact_plane():
+    ds, (At, Bt, Ct) = _exact_plane()
+    nb = (np.array([0, len(ds["h"])], np.int64), np.arange(len(ds["h"]), dtype=np.int32),
+          np.float32([100.0]), np.array([0, 700], np.int64), np.float32([1.0 / 256]))
+    lo = np.array([0.0, -2.0 ** -16, 0.5 * Ct]); hi = np.array([2.0 * At, 2.0 ** -16, 2.0 * Ct])
+    rows = np.array([259, 260, 261])
+    start = np.tile([At * 1.02, 2.0 ** -19, Ct * 0.99], (3, 1))
+    r0 = oracle.crs_refine(ds, nb, start, lo, hi, steps=0, rows=rows)
+    np.testing.assert_array_equal(r0.theta, start)
+    r = oracle.crs_refine(ds, nb, start, lo, hi, steps=40, step0=0.01, rows=rows)
+    assert np.all(r.S >= r0.S)
+    assert np.all(r.theta >= lo) and np.all(r.theta <= hi)
+    assert r.S[1] > 0.999
+
+
+def test_invalid_arguments():
+    ds = dataset([np.zeros(50)], [0.0], 0.004)
+    with pytest.raises(ValueError):
+        oracle.cmp_semblance(ds, [1e-6], w=4)
+    with pytest.raises(ValueError):
+        oracle.cmp_semblance(ds, [1e-6], w=0)
