@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark of the CMP semblance search on GB300 (one JSON line on rank 0).
+
+Workload (default): a 2-D line of 4096 CMP gathers, fold 60, half-offsets 25..3000 m,
+2000 samples at 4 ms, 8 hyperbolic events with a lateral velocity gradient, SNR 1;
+201 candidates C = 4/v^2 for v in 1400..4500 m/s; window w = 11.  One step = one
+cmp_semblance call over all gathers (the whole hot path: traveltime, interpolation,
+semblance, argmax, stack).  The metric is interpolated trace-samples per second
+(intersections x w / s); an intersection is one (gather, t0, candidate, trace) visit.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of
+the same workload (the reference arm of this build: the paper publishes no code).
+Under torchrun (N > 1) every rank processes its own line of 4096 gathers (weak
+scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W = 11
+NC = 201
+VMIN, VMAX = 1400.0, 4500.0
+FLOPS_PER_INTERSECTION = 12 + 7 * W        # the paper's count (Eq. 2)
+SM_MAX_MHZ = 2070.0
+WORKLOAD = "cmp-line: 4096 gathers x fold 60 x 2000 samples @4ms, 201 C candidates, w=11"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _intersections(ds, nc):
+    fold = np.diff(ds["gather_off"])
+    rows = np.diff(ds["out_off"])
+    return int(np.sum(fold.astype(np.int64) * rows.astype(np.int64)) * nc)
+
+
+def _candidates():
+    v = np.linspace(VMIN, VMAX, NC)
+    return (4.0 / v ** 2).astype(np.float32)
+
+
+def _cpu_info():
+    cores = os.cpu_count() or 1
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def oracle_baseline(ds, C, target_s=15.0, seed=0):
+    """Time the FP64 oracle (as it stands) on a seeded sample of output rows, sized for
+    roughly target_s seconds of CPU work.  Returns (trace-samples/s, info)."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    rng = np.random.default_rng(seed)
+    nrows = int(ds["out_off"][-1])
+    fold = int(np.diff(ds["gather_off"]).max())
+    probe = np.sort(rng.choice(nrows, 64, replace=False))
+    t = time.perf_counter()
+    oracle.cmp_semblance(ds, C, w=W, rows=probe, want_cube=False)
+    dt_probe = max(time.perf_counter() - t, 1e-4)
+    per_row = dt_probe / len(probe)
+    n = int(min(nrows, max(64, target_s / per_row)))
+    rows = np.sort(rng.choice(nrows, n, replace=False))
+    t = time.perf_counter()
+    oracle.cmp_semblance(ds, C, w=W, rows=rows, want_cube=False)
+    el = time.perf_counter() - t
+    inter = n * len(C) * fold
+    cores, model = _cpu_info()
+    return inter * W / el, dict(cores=threads, cpu=model, seconds=el,
+                                sample=f"{n} seeded output rows of the workload "
+                                       f"(x {len(C)} candidates x fold {fold}), all traces")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)),
+                    samples=len(sm), reasons=sorted(reasons))
+
+
+def _profile_traffic(kernel_tag):
+    """DRAM traffic per launch from a committed ncu summary, if it was taken on the
+    current kernel source (hash match); else None."""
+    src = sorted(glob.glob(os.path.join(ROOT, "paper_1907_11678_gb300", "csrc", "*")))
+    h = hashlib.sha256()
+    for f in src:
+        h.update(open(f, "rb").read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
+    if not os.path.exists(path):
+        return None, digest
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None, digest
+    if d.get("csrc_sha256_16") != digest:
+        return None, digest
+    return d.get("dram_bytes_per_launch"), digest
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1907_11678_gb300 import build as seis_build
+    from paper_1907_11678_gb300 import seis, synth
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seis_build.build()
+    ds = synth.workload_cmp_line(seed=2 + 1000 * rank)
+    C = _candidates()
+    inter = _intersections(ds, NC)
+    g = seis.to_device(ds, dev)
+    Cd = torch.from_numpy(C).to(dev)
+    out = seis.cmp_semblance(g, Cd, w=W)              # allocate outputs once
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        seis.cmp_semblance(g, Cd, w=W, out=out)
+    torch.cuda.synchronize()
+    seis.device_status()
+
+    # ---- device-resident timing (CUDA events on the launching stream) -----------------
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        seis.cmp_semblance(g, Cd, w=W, out=out)
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    seis.device_status()
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = inter * world * W / (ms_per_step / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ----------------------------------
+    import torch as _t
+    host = {k: _t.from_numpy(np.ascontiguousarray(ds[k])).pin_memory()
+            for k in ("traces", "trace_off", "h", "gather_off", "out_off", "dt")}
+    dev_bufs = {k: _t.empty_like(v, device=dev) for k, v in host.items()}
+    Ch = _t.from_numpy(C).pin_memory()
+    outs_h = {k: _t.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + Ch.numel() * 4
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    g2 = seis.Gathers(traces=dev_bufs["traces"], trace_off=dev_bufs["trace_off"],
+                      h=dev_bufs["h"], m=None, gather_off=dev_bufs["gather_off"],
+                      out_off=dev_bufs["out_off"], dt=dev_bufs["dt"], ngathers=g.ngathers,
+                      ntraces=g.ntraces, max_rows=g.max_rows,
+                      max_trace_samples=g.max_trace_samples, rows=g.rows)
+    Cd2 = _t.empty_like(Cd)
+
+    def e2e_step():
+        for k in host:
+            dev_bufs[k].copy_(host[k], non_blocking=True)
+        Cd2.copy_(Ch, non_blocking=True)
+        seis.cmp_semblance(g2, Cd2, w=W, out=out)
+        for k in out:
+            outs_h[k].copy_(out[k], non_blocking=True)
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    # results of the e2e path equal the device-resident ones
+    assert np.array_equal(outs_h["best_idx"].numpy(), out["best_idx"].cpu().numpy())
+
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak_tflops = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    avg_kernel_s = float(np.mean(kern_ms)) / 1e3
+    achieved = inter * FLOPS_PER_INTERSECTION / avg_kernel_s / 1e12
+    traffic, digest = _profile_traffic("search_kernel_cmp_line")
+    line = {
+        "metric": "CMP semblance interpolated trace-samples/s",
+        "value": value,
+        "unit": "trace-samples/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded CMP line, Ricker 25 Hz events, Gaussian noise SNR 1)",
+        "config": {"workload": WORKLOAD, "gathers_per_gpu": g.ngathers, "fold": 60,
+                   "samples": 2000, "candidates": NC, "w": W,
+                   "intersections_per_step": inter * world,
+                   "l2": "inputs larger than L2 (1.97 GB of traces per GPU)",
+                   "parallelism": f"gathers sharded, dp{world}" if world > 1 else "1 GPU"},
+        "intersections_per_s": inter * world / (ms_per_step / 1e3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": traffic,
+                     "flops_per_intersection": FLOPS_PER_INTERSECTION,
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
+                     "kernel": "search_kernel<CMP, w=11>", "csrc_sha256_16": digest},
+        "e2e": {"value": inter * world * W / (e2e_ms / 1e3), "unit": "trace-samples/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, info = oracle_baseline(ds, C, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "trace-samples/s", "cores": info["cores"],
+                                "kind": "oracle", "sample": info["sample"],
+                                "cpu": info["cpu"], "seconds": info["seconds"]}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    from paper_1907_11678_gb300 import synth
+    ds = synth.workload_cmp_line()
+    C = _candidates()
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        v, info = oracle_baseline(ds, C, target_s=args.ref_seconds, seed=i)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    inter_per_row = NC * 60
+    line = {
+        "impl": "reference",
+        "metric": "CMP semblance interpolated trace-samples/s",
+        "value": value,
+        "unit": "trace-samples/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * 2000 * inter_per_row * W / value,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded CMP line, Ricker 25 Hz events, Gaussian noise SNR 1)",
+        "config": {"workload": WORKLOAD, "gathers_per_gpu": 4096, "fold": 60, "samples": 2000,
+                   "candidates": NC, "w": W, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "trace-samples/s", "cores": info["cores"],
+                         "kind": "oracle", "sample": info["sample"], "cpu": info["cpu"]},
+        "e2e": {"value": value, "unit": "trace-samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

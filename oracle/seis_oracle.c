@@ -114,7 +114,8 @@ static double semblance_of(const double* num, int w, double den, int64_t N)
 
 /* Parity bookkeeping for FP32 implementations: a (row, candidate) is flagged when some
  * trace's participation would change if u moved by +-eps samples (a mask edge sitting
- * on an interpolation knot); see the design notes' reading c5. */
+ * on an interpolation knot).  Traces with zero moveout (h = 0, dm = 0) are exempt from
+ * the flag: their traveltime is exactly t0 in any precision. */
 static int edge_sensitive(double u, int64_t ns, int hw, double eps)
 {
     return window_inside(u - eps, ns, hw) != window_inside(u + eps, ns, hw);
@@ -188,7 +189,8 @@ int seis_oracle_cmp(const float* traces, const int64_t* trace_off, const float* 
                 const double rad = t0 * t0 + Cc * hi * hi;            /* t^2, Section 2.1 */
                 if (!(rad >= 0.0)) continue;
                 const double u = sqrt(rad) / dtg;                      /* traveltime in samples */
-                if (edge && edge_sensitive(u, ns_i, hw, knot_eps)) flag = 1;
+                /* zero moveout (h = 0) lands exactly on sample n in any precision */
+                if (edge && hi != 0.0 && edge_sensitive(u, ns_i, hw, knot_eps)) flag = 1;
                 N += intersect(traces + trace_off[i], ns_i, u, hw, num, &den, &ac);
             }
             const double s = semblance_of(num, w, den, N);
@@ -304,7 +306,8 @@ int seis_oracle_crs(const float* traces, const int64_t* trace_off, const float* 
                         flag = 1;
                 }
                 if (!crs_time(t0, Av, Bv, Cv, dm, (double)h[i], dtg, &u, &p, NULL)) continue;
-                if (edge && edge_sensitive(u, ns_i, hw, knot_eps)) flag = 1;
+                if (edge && (dm != 0.0 || h[i] != 0.0f) && edge_sensitive(u, ns_i, hw, knot_eps))
+                    flag = 1;
                 N += intersect(traces + trace_off[i], ns_i, u, hw, num, &den, &ac);
             }
             const double s = semblance_of(num, w, den, N);

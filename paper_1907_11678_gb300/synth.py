@@ -80,18 +80,23 @@ def _noise_sigma(block_g, snr):
     return sig
 
 
-def _finish(traces64, snr, seed, G, per_gather_len, blk0=0):
-    """Add seeded noise gather-block-wise and return float32."""
-    out = np.empty(traces64.size, np.float32)
-    L = per_gather_len
+def _render(G, M, ns, dt, snr, seed, event_fn):
+    """Render G gathers of M traces x ns samples block by block (bounded memory):
+    event_fn(g0, g1) -> (times [E, (g1-g0)*M], amps [E, (g1-g0)*M]); then add seeded
+    Gaussian noise at the given SNR (None: no noise).  Returns float32 [G*M*ns]."""
+    out = np.empty(G * M * ns, np.float32)
+    L = M * ns
     for b0 in range(0, G, _BLOCK):
         b1 = min(G, b0 + _BLOCK)
-        blk = traces64[b0 * L:b1 * L].reshape(b1 - b0, L)
+        times, amps = event_fn(b0, b1)
+        blk = np.zeros(((b1 - b0) * M, ns))
+        if len(times):
+            _add_events_uniform(blk, np.asarray(times), np.asarray(amps), dt)
+        blk = blk.reshape(b1 - b0, L)
         if snr is not None and snr > 0:
             sig = _noise_sigma(blk, snr)
-            rng = np.random.default_rng([seed, blk0 + b0 // _BLOCK])
-            noise = rng.standard_normal((b1 - b0, L))
-            blk = blk + noise * sig[:, None]
+            rng = np.random.default_rng([seed, b0 // _BLOCK])
+            blk += rng.standard_normal((b1 - b0, L), dtype=np.float32) * sig[:, None]
         out[b0 * L:b1 * L] = blk.reshape(-1)
     return out
 
@@ -110,14 +115,16 @@ def cmp_line(G, M, ns, dt, hmin, hmax, n_events, snr, seed, t0_range=None,
     v0 = rng.uniform(*v_range, size=n_events)
     amp = rng.uniform(*amp_range, size=n_events) * rng.choice([-1.0, 1.0], size=n_events)
     h = np.linspace(hmin, hmax, M)
+
+    def events(g0, g1):
+        g = np.arange(g0, g1)
+        vel = v0[:, None] + v_gradient * (g[None, :] - G / 2.0)       # [E, gathers]
+        tt = np.sqrt(t0[:, None, None] ** 2 + 4.0 * h[None, None, :] ** 2 / vel[:, :, None] ** 2)
+        times = tt.reshape(n_events, (g1 - g0) * M)
+        return times, np.repeat(amp[:, None], (g1 - g0) * M, axis=1)
+
+    traces = _render(G, M, ns, dt, snr, seed, events)
     g = np.arange(G)
-    vel = v0[:, None] + v_gradient * (g[None, :] - G / 2.0)           # [E, G]
-    tt = np.sqrt(t0[:, None, None] ** 2 + 4.0 * h[None, None, :] ** 2 / vel[:, :, None] ** 2)
-    times = tt.reshape(n_events, G * M)
-    amps = np.repeat(amp[:, None], G * M, axis=1)
-    block = np.zeros((G * M, ns))
-    _add_events_uniform(block, times, amps, dt)
-    traces = _finish(block.reshape(-1), snr, seed, G, M * ns)
     trace_off, gather_off, out_off = _layout(np.full(G * M, ns), np.full(G, M), np.full(G, ns))
     return dict(traces=traces, trace_off=trace_off,
                 h=np.tile(h, G).astype(np.float32),
@@ -138,29 +145,38 @@ def crs_line(G, M, ns, dt, hmin, hmax, n_planes, n_diffractors, snr, seed, dm=12
     h = np.linspace(hmin, hmax, M)
     Mm = np.repeat(mid, M)
     Hh = np.tile(h, G)
-    times, amps, planes, diffs = [], [], [], []
+    planes, diffs = [], []
     for _ in range(n_planes):
         t0c = rng.uniform(0.3, 0.85 * T)
         v = rng.uniform(*v_range)
         a = np.deg2rad(rng.uniform(-max_dip_deg, max_dip_deg))
         amp = rng.uniform(*amp_range) * rng.choice([-1.0, 1.0])
-        t0m = t0c + 2.0 * np.sin(a) * (Mm - mcen) / v
-        t = np.where(t0m > 0, np.sqrt(np.maximum(t0m, 0) ** 2 + 4.0 * np.cos(a) ** 2 * Hh ** 2 / v ** 2),
-                     np.nan)
-        times.append(t); amps.append(np.full(G * M, amp))
         planes.append(dict(t0c=t0c, v=v, dip=a, amp=amp, mc=mcen))
     for _ in range(n_diffractors):
         v = rng.uniform(*v_range)
         xd = rng.uniform(mid[0], mid[-1])
         zd = rng.uniform(0.3, 0.8 * T) * v / 2.0
         amp = rng.uniform(*amp_range) * rng.choice([-1.0, 1.0])
-        t = (np.sqrt(zd ** 2 + (Mm - Hh - xd) ** 2) + np.sqrt(zd ** 2 + (Mm + Hh - xd) ** 2)) / v
-        times.append(t); amps.append(np.full(G * M, amp))
         diffs.append(dict(xd=xd, zd=zd, v=v, amp=amp))
-    block = np.zeros((G * M, ns))
-    if times:
-        _add_events_uniform(block, np.array(times), np.array(amps), dt)
-    traces = _finish(block.reshape(-1), snr, seed, G, M * ns)
+
+    def events(g0, g1):
+        mm = Mm[g0 * M:g1 * M]
+        hh = Hh[g0 * M:g1 * M]
+        times, amps = [], []
+        for pl in planes:
+            t0m = pl["t0c"] + 2.0 * np.sin(pl["dip"]) * (mm - mcen) / pl["v"]
+            with np.errstate(invalid="ignore"):
+                t = np.where(t0m > 0, np.sqrt(np.maximum(t0m, 0) ** 2
+                                              + 4.0 * np.cos(pl["dip"]) ** 2 * hh ** 2 / pl["v"] ** 2),
+                             np.nan)
+            times.append(t); amps.append(np.full(len(mm), pl["amp"]))
+        for df in diffs:
+            t = (np.sqrt(df["zd"] ** 2 + (mm - hh - df["xd"]) ** 2)
+                 + np.sqrt(df["zd"] ** 2 + (mm + hh - df["xd"]) ** 2)) / df["v"]
+            times.append(t); amps.append(np.full(len(mm), df["amp"]))
+        return times, amps
+
+    traces = _render(G, M, ns, dt, snr, seed, events)
     trace_off, gather_off, out_off = _layout(np.full(G * M, ns), np.full(G, M), np.full(G, ns))
     return dict(traces=traces, trace_off=trace_off, h=Hh.astype(np.float32),
                 m=Mm.astype(np.float32), gather_off=gather_off, out_off=out_off,

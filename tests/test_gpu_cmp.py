@@ -1,0 +1,134 @@
+"""CMP semblance search on the GPU (through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_11678_gb300 import synth
+from tests import parity
+from tests.dsutil import dataset, pythagorean_offsets, spike_wavelet
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def seis():
+    from paper_1907_11678_gb300 import build, seis as s
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return s
+
+
+def _grid(nc, vmin=1400.0, vmax=4500.0):
+    return oracle.velocity_grid(vmin, vmax, nc).astype(np.float32)
+
+
+def _run(seis, ds, C, w=11, cube=True):
+    g = seis.to_device(ds)
+    out = seis.cmp_semblance(g, torch.from_numpy(C).cuda(), w=w, want_cube=cube)
+    torch.cuda.synchronize()
+    seis.device_status()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _check_all(seis, ds, C, w=11, label="", max_exempt=parity.MAX_EXEMPT_SMALL):
+    got = _run(seis, ds, C, w)
+    ref = oracle.cmp_semblance(ds, C, w=w)
+    rep = parity.check_cube(got["S"], ref, label, max_exempt=max_exempt)
+    row_edge = (ref.edge != 0).any(axis=1)
+    rep.update(parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, label,
+                                  row_edge=row_edge))
+    np.testing.assert_array_equal(got["best_C"], C[got["best_idx"]])
+    return got, ref, rep
+
+
+def test_cmp_small_workload_full_cube(seis):
+    """16 gathers x fold 24 x 1000 samples, 101 candidates, w = 11 (full cube)."""
+    ds = synth.workload_cmp_small()
+    got, ref, rep = _check_all(seis, ds, _grid(101), label="cmp-small",
+                               max_exempt=parity.MAX_EXEMPT)
+    assert rep["pick_agree"] > 0.99
+
+
+@pytest.mark.parametrize("w", [1, 3, 5, 7, 9, 13, 15])
+def test_cmp_windows(seis, w):
+    ds = synth.cmp_line(3, 13, 333, 0.004, 0.0, 1800.0, 3, 1.5, seed=100 + w)
+    _check_all(seis, ds, _grid(37), w=w, label=f"w{w}")
+
+
+@pytest.mark.parametrize("nc", [1, 3, 8, 33, 45, 64])
+def test_cmp_candidate_counts(seis, nc):
+    ds = synth.cmp_line(2, 11, 160, 0.004, 0.0, 1500.0, 2, 2.0, seed=200 + nc)
+    _check_all(seis, ds, _grid(nc), label=f"nc{nc}")
+
+
+def test_cmp_ragged_gathers_and_traces(seis):
+    """Gathers of different fold, output length and dt; traces of different lengths
+    inside one gather; an empty gather; a fold-1 gather."""
+    rng = np.random.default_rng(7)
+    traces, h, sizes, outs, dts = [], [], [], [], []
+    spec = [(9, 77, 0.004), (0, 40, 0.004), (1, 130, 0.002), (17, 301, 0.002), (5, 33, 0.004)]
+    for fold, ns, dt in spec:
+        for i in range(fold):
+            L = ns + int(rng.integers(-20, 25)) if fold > 1 else ns
+            traces.append(rng.standard_normal(max(L, 1)).astype(np.float32))
+            h.append(rng.uniform(0, 1600))
+        sizes.append(fold); outs.append(ns); dts.append(dt)
+    ds = dataset(traces, h, 0.0, gather_sizes=sizes, out_ns=outs)
+    ds["dt"] = np.float32(dts)
+    got, ref, rep = _check_all(seis, ds, _grid(29), label="ragged")
+    o = ds["out_off"]
+    empty = slice(o[1], o[2])
+    assert np.all(got["S"][empty] == 0) and np.all(got["stack"][empty] == 0)
+    assert np.all(got["best_idx"][empty] == 0)
+
+
+def test_cmp_constant_and_zero(seis):
+    ns, M = 200, 10
+    ds = dataset([np.full(ns, 0.75, np.float32)] * M + [np.zeros(ns, np.float32)] * M,
+                 list(np.linspace(0, 1500, M)) * 2, 0.004, gather_sizes=[M, M])
+    got = _run(seis, ds, _grid(40))
+    ref = oracle.cmp_semblance(ds, _grid(40))
+    has = ref.N[:ns] > 0
+    np.testing.assert_allclose(got["S"][:ns][has], 1.0, atol=1e-6)
+    assert np.all(got["S"][:ns][~has] == 0)
+    assert np.all(got["S"][ns:] == 0) and np.all(got["stack"][ns:] == 0)
+
+
+def test_cmp_exact_hyperbola(seis):
+    n0, ns, dt, Ct = 240, 700, 1.0 / 256.0, 2.0 ** -20
+    trip = [(0, n0)] + pythagorean_offsets(n0, 150)
+    ds = dataset([spike_wavelet(ns, mm, 2.5) for _, mm in trip], [16.0 * a for a, _ in trip], dt)
+    C = np.float32(Ct * np.array([0.5, 0.8, 0.9, 1.0, 1.1, 1.25, 1.6]))
+    got = _run(seis, ds, C)
+    assert got["S"][n0, 3] == pytest.approx(1.0, abs=1e-5)
+    assert got["best_idx"][n0] == 3
+
+
+def test_cmp_deterministic(seis):
+    ds = synth.cmp_line(4, 20, 500, 0.004, 0.0, 2000.0, 4, 1.0, seed=9)
+    a = _run(seis, ds, _grid(77))
+    b = _run(seis, ds, _grid(77))
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.slow
+def test_cmp_line_full_size_sampled(seis):
+    """The benchmark workload at full size (4096 gathers x fold 60 x 2000 samples, 201
+    candidates, w = 11, no cube) in the launch configuration the benchmark times; the
+    oracle checks a seeded sample of rows."""
+    ds = synth.workload_cmp_line()
+    C = _grid(201)
+    got = _run(seis, ds, C, cube=False)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(int(ds["out_off"][-1]), 768, replace=False))
+    rows = np.concatenate([rows, [0, 1999, 2000, 8191999]])
+    ref = oracle.cmp_semblance(ds, C, rows=rows)
+    sub = {k: got[k][rows] for k in ("best_idx", "best_S", "stack")}
+    row_edge = (ref.edge != 0).any(axis=1)
+    rep = parity.check_picks(sub["best_idx"], sub["best_S"], sub["stack"], ref, "cmp-line",
+                             row_edge=row_edge)
+    assert rep["pick_agree"] > 0.98
+    assert np.all(got["best_S"] >= 0) and np.all(got["best_S"] <= 1.0 + 1e-5)
