@@ -176,7 +176,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     seis_build.build()
-    ds = synth.workload_cmp_line(seed=2 + 1000 * rank)
+    ds = synth.workload_cmp_line(seed=2 + 1000 * rank, G=args.gathers)
     C = _candidates()
     inter = _intersections(ds, NC)
     g = seis.to_device(ds, dev)
@@ -220,7 +220,28 @@ def run_ours(args):
     value = inter * world * W / (ms_per_step / 1e3)
 
     # ---- end to end through the C ABI with host buffers ----------------------------------
+    e2e = None
+    if not args.skip_e2e:
+        e2e = _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream)
+    line = _line(args, ds, g, inter, world, ms_per_step, value, kern_ms, clk, e2e, dev)
+    if rank == 0 and not args.no_cpu_baseline:
+        v, info = oracle_baseline(ds, C, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "trace-samples/s", "cores": info["cores"],
+                                "kind": "oracle", "sample": info["sample"],
+                                "cpu": info["cpu"], "seconds": info["seconds"]}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream):
+    """Same metric through the C ABI with the step's inputs copied from pinned host
+    memory and its results copied back inside the timed region."""
     import torch as _t
+    import torch.distributed as dist
+    from paper_1907_11678_gb300 import seis
     host = {k: _t.from_numpy(np.ascontiguousarray(ds[k])).pin_memory()
             for k in ("traces", "trace_off", "h", "gather_off", "out_off", "dt")}
     dev_bufs = {k: _t.empty_like(v, device=dev) for k, v in host.items()}
@@ -244,16 +265,16 @@ def run_ours(args):
             outs_h[k].copy_(out[k], non_blocking=True)
     for _ in range(max(1, args.warmup)):
         e2e_step()
-    torch.cuda.synchronize()
+    _t.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    e0 = _t.cuda.Event(enable_timing=True)
+    e1 = _t.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         e2e_step()
     e1.record(stream)
-    torch.cuda.synchronize()
+    _t.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         tt = torch.tensor([e2e_ms], device=dev)
@@ -261,14 +282,24 @@ def run_ours(args):
         e2e_ms = float(tt.item())
     # results of the e2e path equal the device-resident ones
     assert np.array_equal(outs_h["best_idx"].numpy(), out["best_idx"].cpu().numpy())
+    return {"value": inter * world * W / (e2e_ms / 1e3), "unit": "trace-samples/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": e2e_ms}
 
+
+def _line(args, ds, g, inter, world, ms_per_step, value, kern_ms, clk, e2e, dev):
+    import torch
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peak_tflops = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
     avg_kernel_s = float(np.mean(kern_ms)) / 1e3
     achieved = inter * FLOPS_PER_INTERSECTION / avg_kernel_s / 1e12
     traffic, digest = _profile_traffic("search_kernel_cmp_line")
-    line = {
+    if traffic is not None:
+        traffic = traffic * g.ngathers / 4096.0
+    workload = WORKLOAD if g.ngathers == 4096 else \
+        WORKLOAD.replace("4096 gathers", f"{g.ngathers} gathers (profiling size)")
+    return {
         "metric": "CMP semblance interpolated trace-samples/s",
         "value": value,
         "unit": "trace-samples/s",
@@ -281,7 +312,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded CMP line, Ricker 25 Hz events, Gaussian noise SNR 1)",
-        "config": {"workload": WORKLOAD, "gathers_per_gpu": g.ngathers, "fold": 60,
+        "config": {"workload": workload, "gathers_per_gpu": g.ngathers, "fold": 60,
                    "samples": 2000, "candidates": NC, "w": W,
                    "intersections_per_step": inter * world,
                    "l2": "inputs larger than L2 (1.97 GB of traces per GPU)",
@@ -293,22 +324,10 @@ def run_ours(args):
                      "flops_per_intersection": FLOPS_PER_INTERSECTION,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
                      "kernel": "search_kernel<CMP, w=11>", "csrc_sha256_16": digest},
-        "e2e": {"value": inter * world * W / (e2e_ms / 1e3), "unit": "trace-samples/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": e2e_ms},
+        "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        v, info = oracle_baseline(ds, C, target_s=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "trace-samples/s", "cores": info["cores"],
-                                "kind": "oracle", "sample": info["sample"],
-                                "cpu": info["cpu"], "seconds": info["seconds"]}
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -360,6 +379,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--gathers", type=int, default=4096,
+                    help="gathers per GPU (4096 = the benchmark workload; fewer only for profiling)")
+    ap.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -6,24 +6,27 @@
 // linear stack), Section 3.2 (argmax over candidates, stack at the pick), and for CRS
 // Section 2.2 / 3.5 (the aperture's traces and the A/B/C traveltime surface).
 //
-// How (GB300 design; the paper's Algorithm 2 "re-design" idea of reusing one staged
-// trace window for many (t0, candidate) pairs, realised with the TMA engine):
+// How (GB300 design; it keeps the paper's Algorithm 2 idea -- one staged trace window
+// reused by many (t0, candidate) pairs -- and realises it with the TMA engine):
 //   - one CTA = one owner (CMP gather or CRS central CDP) x 32 consecutive output rows;
-//     lane l of every warp owns row n0 + l, so the 32 lanes of a warp read 32 nearby
-//     sample indices of the same trace (no bank conflicts, often broadcasts);
-//   - candidates are processed in passes of 32: each thread keeps the accumulators of 4
-//     candidates (num[w], den, N) in registers for the whole trace loop;
-//   - per pass, traces stream through a double-buffered shared-memory ring in stages of
-//     up to 64 traces: warp 0 computes, for every trace, the exact sample window that the
-//     stage's 32 rows x 32 candidates can touch (traveltime bounds at the box corners,
-//     +-2 samples of margin), and copies it with one 1-D bulk copy (cp.async.bulk) plus
-//     at most 3+3 scalar edge loads; completion is tracked by an mbarrier transaction
-//     count, so the next stage loads while the current one computes;
+//     lane l of every consumer warp owns row n0 + l, so the 32 lanes of a warp read 32
+//     nearby sample indices of the same trace (conflict-free, often broadcast);
+//   - candidates are processed in passes of 28; a consumer thread keeps 4 candidates'
+//     accumulators (num[w], den, N) in registers through the whole trace loop, as two
+//     packed pairs updated with Blackwell's fma/add.rn.f32x2 (two FP32 lanes per issue);
+//   - a dedicated producer warp streams, per pass, the traces through a 4-slot
+//     shared-memory ring in stages of up to 32 traces: for every trace it computes the
+//     exact sample window the stage's 32 rows x 28 candidates can touch (traveltime
+//     bounds at the box corners, +-2 samples of margin) and copies it with one 1-D bulk
+//     copy (cp.async.bulk) plus at most 3+3 scalar edge loads; "full" mbarriers count the
+//     bytes, "empty" mbarriers return the slot; no block-wide barrier in the loop;
 //   - the traveltime is formed in sample units as u = n + D with the cancellation-free
-//     moveout D = C q / (sqrt(n^2 + C q) + n), q = (h/dt)^2, which keeps the
-//     interpolation fraction accurate to ~1e-4 samples in FP32;
+//     moveout D = C q / (sqrt(n^2 + C q) + n), q = (h/dt)^2 (CRS: D = a + r/(s + p)),
+//     which keeps the interpolation fraction accurate to ~1e-4 samples in FP32;
+//   - the inner loop is branch-free: a pair whose trace does not take part reads a
+//     zero strip and adds nothing;
 //   - the argmax over all candidates stays inside the CTA (register running best per
-//     thread, then an 8-way shared-memory reduction), so no atomics and no cube.
+//     thread, then a 7-way shared-memory reduction), so no atomics and no cube.
 #pragma once
 #include <cfloat>
 #include <climits>
@@ -32,17 +35,21 @@
 
 namespace seis {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = 32 * kWarps;
-constexpr int kR = 4;                  // candidates per thread per pass
-constexpr int kCB = kWarps * kR;       // candidates per pass (= 32: one per planner lane)
-constexpr int kChunkT = 64;            // traces per stage at most
-constexpr int kBuf = 12288;            // floats per stage buffer (48 KB)
+constexpr int kWarps = 7;                    // consumer warps (7 + 1 = 8 warps: 2 CTAs fill
+                                             // the 4 sub-partitions evenly at 128 registers)
+constexpr int kThreads = 32 * (kWarps + 1);  // + one producer warp
+constexpr int kConsumers = 32 * kWarps;
+constexpr int kR = 4;                        // candidates per consumer thread per pass
+constexpr int kCB = kWarps * kR;             // candidates per pass (28 <= producer lanes)
+constexpr int kChunkT = 32;                  // traces per stage at most (one per producer lane)
+constexpr int kSlots = 4;                    // ring depth
+constexpr int kBuf = 6144;                   // floats per slot (24 KB)
 constexpr unsigned kFull = 0xffffffffu;
+static_assert(kCB <= 32, "the producer bounds one candidate per lane");
 
 struct __align__(16) TraceMeta {
-    int base;     // shared-memory float index of sample 0 of the trace in this stage's buffer
-    int kmin;     // intersections with kmin <= k <= kmax take part (window inside trace,
+    int base;     // shared-memory float index of sample 0 of the trace in its slot buffer
+    int kmin;     // intersections with kmin <= k <= kmax take part (window inside the trace
     int kmax;     //   and inside the staged sample window)
     float q;      // (h/dt)^2
     float e;      // dm/dt            (CRS)
@@ -55,16 +62,45 @@ struct __align__(16) StageDesc {
 };
 
 struct SearchSmem {
-    float buf[2][kBuf];
-    TraceMeta meta[2][kChunkT];
-    StageDesc desc[2];
-    uint64_t full[2];
+    float buf[kSlots][kBuf];
+    TraceMeta meta[kSlots][kChunkT];
+    StageDesc desc[kSlots];
+    uint64_t full[kSlots];
+    uint64_t empty[kSlots];
+    float zeros[16];
     int abort_flag;
     int pad[3];
     float redS[kWarps][32];
     int redC[kWarps][32];
     float redT[kWarps][32];
 };
+
+// ---- packed FP32 pairs (Blackwell f32x2) -------------------------------------------
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t pk2(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void up2(f2_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 __device__ __forceinline__ float warp_min(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
@@ -73,6 +109,10 @@ __device__ __forceinline__ float warp_min(float v) {
 __device__ __forceinline__ float warp_max(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
     return v;
+}
+
+__device__ __forceinline__ void consumer_bar() {
+    asm volatile("bar.sync 1, %0;" :: "r"(kConsumers) : "memory");
 }
 
 template <bool CRS>
@@ -94,6 +134,35 @@ __device__ __forceinline__ void decode_candidate(const SearchParams& P, int c, f
     }
 }
 
+// One intersection's traveltime -> (window start pointer, fraction, takes part).
+template <bool CRS>
+__device__ __forceinline__ void intersect_setup(float A, float B, float C, const TraceMeta& tm,
+                                                int n, float nf, float n2, bool act,
+                                                const float* fb, const float* zeros,
+                                                const float*& p, float& x, bool& ok) {
+    float D;
+    if (CRS) {
+        const float a = A * tm.e;
+        const float pp = nf + a;
+        const float rr = fmaf(B, tm.g, C * tm.q);
+        const float rad = fmaf(pp, pp, rr);
+        const float s = sqrt_fast(rad);
+        D = fmaf(rr, rcp_fast(fmaxf(s + pp, 1e-30f)), a);
+        ok = act && (pp >= 0.f) && (rad >= 0.f);
+    } else {
+        const float cq = C * tm.q;
+        const float rad = n2 + cq;
+        const float s = sqrt_fast(rad);
+        D = cq * rcp_fast(fmaxf(s + nf, 1e-30f));
+        ok = act && (rad >= 0.f);
+    }
+    const float fl = floorf(D);
+    const int k = n + __float2int_rz(fminf(fl, 16777216.f));
+    ok = ok && (k >= tm.kmin) && (k <= tm.kmax);
+    x = ok ? (D - fl) : 0.f;
+    p = ok ? (fb + k) : zeros;
+}
+
 template <bool CRS, int W>
 __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams P) {
     constexpr int HW = W / 2;
@@ -113,48 +182,56 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
     const int64_t M64 = P.list_off[owner + 1] - lbeg;
     const int M = M64 < 0 ? 0 : (M64 > INT_MAX ? INT_MAX : (int)M64);
     const float dt = P.dt[owner];
-    const float mc = CRS ? P.m_c[owner] : 0.f;
     const int npass = (P.ncand + kCB - 1) / kCB;
-    const int n = n0 + lane;
-    const bool act = n < nrows;
-    const int n_last = min(n0 + 31, nrows - 1);
 
     if (threadIdx.x == 0) {
-        mbar_init(&sm.full[0], 32);
-        mbar_init(&sm.full[1], 32);
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(&sm.full[s], 32);           // the producer warp's lanes
+            mbar_init(&sm.empty[s], kConsumers);  // every consumer thread
+        }
         sm.abort_flag = 0;
         fence_mbar_init();
     }
+    if (threadIdx.x < 16) sm.zeros[threadIdx.x] = 0.f;
     __syncthreads();
 
-    // ---------------- planner (warp 0): stage sequence = passes x trace chunks ----------
-    int pl_pass = 0, pl_t = 0, pl_bpass = -1;
-    float bA0 = 0.f, bA1 = 0.f, bB0 = 0.f, bB1 = 0.f, bC0 = 0.f, bC1 = 0.f;
-
-    auto plan = [&](int slot) {
-        if (pl_pass >= npass) {
-            if (lane == 0) sm.desc[slot] = StageDesc{0, 0, 0, 0, 1, 0, 0, 0};
+    if (warp == kWarps) {
+        // =============================== producer warp ================================
+        const float mc = CRS ? P.m_c[owner] : 0.f;
+        const int n_last = min(n0 + 31, nrows - 1);
+        int pl_pass = 0, pl_t = 0, pl_bpass = -1;
+        float bA0 = 0.f, bA1 = 0.f, bB0 = 0.f, bB1 = 0.f, bC0 = 0.f, bC1 = 0.f;
+        int s = 0;
+        for (;; ++s) {
+            const int slot = s % kSlots;
+            if (s >= kSlots && !sm.abort_flag) {
+                if (!mbar_wait_bounded(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
+                    sm.abort_flag = 1;
+                    record_status(P.status, kStatusTimeout);
+                }
+            }
             __syncwarp();
-            mbar_arrive(&sm.full[slot]);
-            return;
-        }
-        if (pl_bpass != pl_pass) {   // candidate bounds of this pass (one candidate per lane)
-            const int c = pl_pass * kCB + lane;
-            float a = 0.f, b = 0.f, cc = 0.f;
-            const bool v = c < P.ncand;
-            if (v) decode_candidate<CRS>(P, c, a, b, cc);
-            bA0 = warp_min(v ? a : FLT_MAX);  bA1 = warp_max(v ? a : -FLT_MAX);
-            bB0 = warp_min(v ? b : FLT_MAX);  bB1 = warp_max(v ? b : -FLT_MAX);
-            bC0 = warp_min(v ? cc : FLT_MAX); bC1 = warp_max(v ? cc : -FLT_MAX);
-            pl_bpass = pl_pass;
-        }
-        float* slotbuf = sm.buf[slot];
-        const int first = (pl_t == 0);
-        int cnt = 0, used = 0;
-        fence_proxy_async_smem();    // earlier generic accesses of this slot before async writes
-        while (cnt < kChunkT && pl_t < M) {
+            if (sm.abort_flag || pl_pass >= npass) {
+                if (lane == 0) sm.desc[slot] = StageDesc{0, 0, 0, 0, 1, 0, 0, 0};
+                __syncwarp();
+                mbar_arrive(&sm.full[slot]);
+                break;
+            }
+            if (pl_bpass != pl_pass) {   // candidate bounds of this pass (one per lane)
+                const int c = pl_pass * kCB + lane;
+                float a = 0.f, b = 0.f, cc = 0.f;
+                const bool v = lane < kCB && c < P.ncand;
+                if (v) decode_candidate<CRS>(P, c, a, b, cc);
+                bA0 = warp_min(v ? a : FLT_MAX);  bA1 = warp_max(v ? a : -FLT_MAX);
+                bB0 = warp_min(v ? b : FLT_MAX);  bB1 = warp_max(v ? b : -FLT_MAX);
+                bC0 = warp_min(v ? cc : FLT_MAX); bC1 = warp_max(v ? cc : -FLT_MAX);
+                pl_bpass = pl_pass;
+            }
+            float* slotbuf = sm.buf[slot];
+            const int first = (pl_t == 0);
+            fence_proxy_async_smem();   // earlier generic accesses of the slot before async writes
             const int t = pl_t + lane;
-            const bool v = (t < M) && (cnt + lane < kChunkT);
+            const bool v = t < M;
             int len = 0, n_el = 0, mis = 0, lo = 0;
             const float* src = nullptr;
             TraceMeta tm{0, 1, 0, 0.f, 0.f, 0.f, 0, 0};
@@ -186,10 +263,8 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
                 if (pHi >= 0.f && radHi >= 0.f) {
                     const float uLo = fminf(sqrtf(fmaxf(radLo, 0.f)), 1.6e7f);
                     const float uHi = fminf(sqrtf(radHi), 1.6e7f);
-                    const int klo = (int)floorf(uLo) - 2;
-                    const int khi = (int)floorf(uHi) + 2;
-                    const int kmin = max(klo, HW);
-                    const int kmax = min(khi, ns_i - HW - 2);
+                    const int kmin = max((int)floorf(uLo) - 2, HW);
+                    const int kmax = min((int)floorf(uHi) + 2, ns_i - HW - 2);
                     if (kmin <= kmax) {
                         tm.kmin = kmin;
                         tm.kmax = kmax;
@@ -201,76 +276,80 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
                     }
                 }
             }
-            int pre = len;                                       // inclusive scan of lengths
+            int pre = len;                                     // inclusive scan of lengths
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(kFull, pre, o);
                 if (lane >= o) pre += y;
             }
-            const bool fits = v && (used + pre <= kBuf);
-            const int nfit = __popc(__ballot_sync(kFull, fits));  // a prefix of the lanes
-            if (nfit == 0) {
-                if (cnt == 0) {      // a single window larger than the buffer: drop + flag
-                    if (lane == 0) {
-                        record_status(P.status, kStatusOverflow);
-                        sm.meta[slot][0] = TraceMeta{0, 1, 0, 0.f, 0.f, 0.f, 0, 0};
-                    }
-                    cnt = 1;
-                    pl_t += 1;
-                    continue;
+            const bool fits = v && (pre <= kBuf);
+            int nfit = __popc(__ballot_sync(kFull, fits));    // a prefix of the lanes
+            if (nfit == 0 && M > pl_t) {
+                // a single window larger than a slot (traces are limited on the host so this
+                // cannot happen): drop that trace for this pass and record it
+                if (lane == 0) {
+                    record_status(P.status, kStatusOverflow);
+                    sm.meta[slot][0] = TraceMeta{0, 1, 0, 0.f, 0.f, 0.f, 0, 0};
                 }
-                break;
-            }
-            if (lane < nfit) {
-                const int off = used + pre - len;                  // multiple of 4 floats
+                nfit = 1;
+            } else if (lane < nfit) {
+                const int off = pre - len;                       // multiple of 4 floats
                 tm.base = off + mis - lo;
-                sm.meta[slot][cnt + lane] = tm;
+                sm.meta[slot][lane] = tm;
                 if (n_el > 0) {
                     float* dst = slotbuf + off + mis;
                     const int head = min((4 - mis) & 3, n_el);
                     const int nb = (n_el - head) & ~3;
-                    for (int e2 = 0; e2 < head; ++e2) dst[e2] = ldg_nc(src + e2);
-                    for (int e2 = head + nb; e2 < n_el; ++e2) dst[e2] = ldg_nc(src + e2);
                     if (nb > 0) {
                         mbar_expect_tx(&sm.full[slot], (uint32_t)nb * 4u);
                         bulk_g2s(dst + head, src + head, (uint32_t)nb * 4u, &sm.full[slot]);
                     }
+                    for (int e2 = 0; e2 < head; ++e2) dst[e2] = ldg_nc(src + e2);
+                    for (int e2 = head + nb; e2 < n_el; ++e2) dst[e2] = ldg_nc(src + e2);
                 }
             }
-            used += __shfl_sync(kFull, pre, nfit - 1);
-            cnt += nfit;
             pl_t += nfit;
+            const int last = (pl_t >= M);
+            if (lane == 0) sm.desc[slot] = StageDesc{pl_pass, nfit, first, last, 0, 0, 0, 0};
+            if (last) { ++pl_pass; pl_t = 0; }
+            __syncwarp();
+            mbar_arrive(&sm.full[slot]);
         }
-        const int last = (pl_t >= M);
-        if (lane == 0) sm.desc[slot] = StageDesc{pl_pass, cnt, first, last, 0, 0, 0, 0};
-        if (last) { ++pl_pass; pl_t = 0; }
-        __syncwarp();
-        mbar_arrive(&sm.full[slot]);
-    };
+        // Let every stage still in flight land before the CTA's shared memory is released.
+        const int s_end = s;
+        for (int s2 = max(0, s_end - kSlots + 1); s2 <= s_end; ++s2)
+            mbar_wait_bounded(&sm.full[s2 % kSlots], (uint32_t)((s2 / kSlots) & 1));
+        return;
+    }
 
-    // ---------------- consumers (all warps) -------------------------------------------
-    float num[kR][W];
-    float den[kR];
+    // ================================ consumer warps =====================================
+    const int n = n0 + lane;
+    const bool act = n < nrows;
+    const float nf = (float)n;
+    const float n2 = nf * nf;
+    f2_t num[kR / 2][W];
+    f2_t den[kR / 2];
     int cntv[kR];
     float Ar[kR], Br[kR], Cr[kR];
     int cidx[kR];
     float bestS = -1.f, bestT = 0.f;
     int bestC = INT_MAX;
-    const float nf = (float)n;
-    const float n2 = nf * nf;
+    bool aborted = false;
+    #pragma unroll
+    for (int r = 0; r < kR; ++r) { cidx[r] = INT_MAX; Ar[r] = Br[r] = Cr[r] = 0.f; cntv[r] = 0; }
 
-    if (warp == 0) { plan(0); plan(1); }
-
-    int it = 0;
-    for (;; ++it) {
-        const int slot = it & 1;
-        if (!sm.abort_flag) {
-            if (!mbar_wait_bounded(&sm.full[slot], (uint32_t)((it >> 1) & 1))) {
-                sm.abort_flag = 1;
-                record_status(P.status, kStatusTimeout);
-            }
+    for (int s = 0;; ++s) {
+        const int slot = s % kSlots;
+        if (!mbar_wait_bounded(&sm.full[slot], (uint32_t)((s / kSlots) & 1))) {
+            sm.abort_flag = 1;
+            record_status(P.status, kStatusTimeout);
+            aborted = true;
+            break;
         }
         const StageDesc d = sm.desc[slot];
-        if (d.end) break;
+        if (d.end) {
+            aborted = sm.abort_flag != 0;
+            break;
+        }
         if (d.first) {
             #pragma unroll
             for (int r = 0; r < kR; ++r) {
@@ -278,98 +357,92 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
                 cidx[r] = c;
                 Ar[r] = Br[r] = Cr[r] = 0.f;
                 if (c < P.ncand) decode_candidate<CRS>(P, c, Ar[r], Br[r], Cr[r]);
-                den[r] = 0.f;
                 cntv[r] = 0;
+            }
+            #pragma unroll
+            for (int r2 = 0; r2 < kR / 2; ++r2) {
+                den[r2] = 0ull;
                 #pragma unroll
-                for (int j = 0; j < W; ++j) num[r][j] = 0.f;
+                for (int j = 0; j < W; ++j) num[r2][j] = 0ull;
             }
         }
         const float* sbuf = sm.buf[slot];
         const int ntr = min(d.ntr, kChunkT);
+        // a pass's second packed pair (r = 2, 3) holds its highest candidates
+        const bool pair1 = cidx[2] < P.ncand;
         for (int t = 0; t < ntr; ++t) {
             const TraceMeta tm = sm.meta[slot][t];
             const float* fb = sbuf + (tm.base - HW);
             #pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                if (cidx[r] >= P.ncand) continue;                  // warp-uniform
-                float D;
-                bool ok;
-                if (CRS) {
-                    const float a = Ar[r] * tm.e;
-                    const float p = nf + a;
-                    const float rr = fmaf(Br[r], tm.g, Cr[r] * tm.q);
-                    const float rad = fmaf(p, p, rr);
-                    const float s = sqrt_fast(rad);
-                    D = fmaf(rr, rcp_fast(fmaxf(s + p, 1e-30f)), a);
-                    ok = act && (p >= 0.f) && (rad >= 0.f);
-                } else {
-                    const float cq = Cr[r] * tm.q;
-                    const float rad = n2 + cq;
-                    const float s = sqrt_fast(rad);
-                    D = cq * rcp_fast(fmaxf(s + nf, 1e-30f));
-                    ok = act && (rad >= 0.f);
+            for (int r2 = 0; r2 < kR / 2; ++r2) {
+                if (r2 == 1 && !pair1) continue;                      // warp-uniform
+                const int ra = 2 * r2, rb = 2 * r2 + 1;
+                const float* pa;
+                const float* pb;
+                float xa, xb;
+                bool oka, okb;
+                intersect_setup<CRS>(Ar[ra], Br[ra], Cr[ra], tm, n, nf, n2, act && cidx[ra] < P.ncand,
+                                     fb, sm.zeros, pa, xa, oka);
+                intersect_setup<CRS>(Ar[rb], Br[rb], Cr[rb], tm, n, nf, n2, act && cidx[rb] < P.ncand,
+                                     fb, sm.zeros, pb, xb, okb);
+                const f2_t x2 = pk2(xa, xb);
+                f2_t F[W + 1];
+                #pragma unroll
+                for (int j = 0; j <= W; ++j) F[j] = pk2(pa[j], pb[j]);
+                f2_t dd = den[r2];
+                #pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    const f2_t v = fma2(x2, sub2(F[j + 1], F[j]), F[j]);
+                    num[r2][j] = add2(num[r2][j], v);
+                    dd = fma2(v, v, dd);
                 }
-                const float fl = floorf(D);
-                const float x = D - fl;
-                const int k = n + __float2int_rz(fminf(fl, 16777216.f));
-                ok = ok && (k >= tm.kmin) && (k <= tm.kmax);
-                if (ok) {
-                    const float* p = fb + k;
-                    float f[W + 1];
-                    #pragma unroll
-                    for (int j = 0; j <= W; ++j) f[j] = p[j];
-                    #pragma unroll
-                    for (int j = 0; j < W; ++j) {
-                        const float v = fmaf(x, f[j + 1] - f[j], f[j]);
-                        num[r][j] += v;
-                        den[r] = fmaf(v, v, den[r]);
-                    }
-                    cntv[r] += 1;
-                }
+                den[r2] = dd;
+                cntv[ra] += oka ? 1 : 0;
+                cntv[rb] += okb ? 1 : 0;
             }
         }
         if (d.last) {
             #pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                const int c = cidx[r];
-                if (c >= P.ncand) continue;
-                float nu = 0.f, ac = 0.f;
+            for (int r2 = 0; r2 < kR / 2; ++r2) {
+                float nuA = 0.f, nuB = 0.f, acA = 0.f, acB = 0.f, dA, dB;
                 #pragma unroll
-                for (int j = 0; j < W; ++j) { nu = fmaf(num[r][j], num[r][j], nu); ac += num[r][j]; }
-                const float Nf = (float)cntv[r];
-                const float s = (cntv[r] > 0 && den[r] > 0.f) ? nu / (Nf * den[r]) : 0.f;
-                const float st = cntv[r] > 0 ? ac / (Nf * (float)W) : 0.f;
-                if (P.S_cube && act) P.S_cube[(row0 + n) * (int64_t)P.ncand + c] = s;
-                if (s > bestS) { bestS = s; bestC = c; bestT = st; }
+                for (int j = 0; j < W; ++j) {
+                    float a, b;
+                    up2(num[r2][j], a, b);
+                    nuA = fmaf(a, a, nuA); acA += a;
+                    nuB = fmaf(b, b, nuB); acB += b;
+                }
+                up2(den[r2], dA, dB);
+                #pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = 2 * r2 + h;
+                    const int c = cidx[r];
+                    if (c >= P.ncand) continue;
+                    const float nu = h ? nuB : nuA, ac = h ? acB : acA, dn = h ? dB : dA;
+                    const float Nf = (float)cntv[r];
+                    const float sv = (cntv[r] > 0 && dn > 0.f) ? nu / (Nf * dn) : 0.f;
+                    const float st = cntv[r] > 0 ? ac / (Nf * (float)W) : 0.f;
+                    if (P.S_cube && act) P.S_cube[(row0 + n) * (int64_t)P.ncand + c] = sv;
+                    if (sv > bestS) { bestS = sv; bestC = c; bestT = st; }
+                }
             }
         }
-        __syncthreads();                         // every consumer is done with this slot
-        if (sm.abort_flag) break;
-        if (warp == 0) plan(slot);
-    }
-
-    if (sm.abort_flag) {
-        // Stages `it` and `it + 1` may still have copies in flight: let them land (bounded)
-        // before the CTA's shared memory is released.
-        if (threadIdx.x == 0) {
-            mbar_wait_bounded(&sm.full[it & 1], (uint32_t)((it >> 1) & 1));
-            mbar_wait_bounded(&sm.full[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1));
-        }
-        return;
+        mbar_arrive(&sm.empty[slot]);                   // this thread is done with the slot
     }
 
     sm.redS[warp][lane] = bestS;
     sm.redC[warp][lane] = bestC;
     sm.redT[warp][lane] = bestT;
-    __syncthreads();
+    consumer_bar();
+    if (aborted || sm.abort_flag) return;
     if (warp == 0 && act) {
         float bs = sm.redS[0][lane], bt = sm.redT[0][lane];
         int bc = sm.redC[0][lane];
         #pragma unroll
         for (int w2 = 1; w2 < kWarps; ++w2) {
-            const float s = sm.redS[w2][lane];
+            const float sv = sm.redS[w2][lane];
             const int c = sm.redC[w2][lane];
-            if (s > bs || (s == bs && c < bc)) { bs = s; bc = c; bt = sm.redT[w2][lane]; }
+            if (sv > bs || (sv == bs && c < bc)) { bs = sv; bc = c; bt = sm.redT[w2][lane]; }
         }
         if (bc == INT_MAX) { bc = 0; bs = 0.f; bt = 0.f; }
         const int64_t row = row0 + n;
