@@ -114,11 +114,17 @@ static double semblance_of(const double* num, int w, double den, int64_t N)
 
 /* Parity bookkeeping for FP32 implementations: a (row, candidate) is flagged when some
  * trace's participation would change if u moved by +-eps samples (a mask edge sitting
- * on an interpolation knot).  Traces with zero moveout (h = 0, dm = 0) are exempt from
- * the flag: their traveltime is exactly t0 in any precision. */
+ * on an interpolation knot). */
 static int edge_sensitive(double u, int64_t ns, int hw, double eps)
 {
     return window_inside(u - eps, ns, hw) != window_inside(u + eps, ns, hw);
+}
+
+/* All moveout terms vanish (A dm = B dm^2 = C h^2 = 0): the traveltime is exactly t0 in
+ * any precision, so such a trace never makes a (row, candidate) parity-sensitive. */
+static int zero_moveout(double A, double B, double C, double dm, double h)
+{
+    return A * dm == 0.0 && B * dm * dm == 0.0 && C * h * h == 0.0;
 }
 
 /* Output row r -> (owner index, local sample n) by binary search in off[0..cnt]. */
@@ -189,8 +195,9 @@ int seis_oracle_cmp(const float* traces, const int64_t* trace_off, const float* 
                 const double rad = t0 * t0 + Cc * hi * hi;            /* t^2, Section 2.1 */
                 if (!(rad >= 0.0)) continue;
                 const double u = sqrt(rad) / dtg;                      /* traveltime in samples */
-                /* zero moveout (h = 0) lands exactly on sample n in any precision */
-                if (edge && hi != 0.0 && edge_sensitive(u, ns_i, hw, knot_eps)) flag = 1;
+                if (edge && !zero_moveout(0.0, 0.0, Cc, 0.0, hi) &&
+                    edge_sensitive(u, ns_i, hw, knot_eps))
+                    flag = 1;
                 N += intersect(traces + trace_off[i], ns_i, u, hw, num, &den, &ac);
             }
             const double s = semblance_of(num, w, den, N);
@@ -300,14 +307,16 @@ int seis_oracle_crs(const float* traces, const int64_t* trace_off, const float* 
                 double u, p;
                 const double rad = (t0 + Av * dm) * (t0 + Av * dm) + Bv * dm * dm
                                    + Cv * (double)h[i] * (double)h[i];
+                const int exact = zero_moveout(Av, Bv, Cv, dm, (double)h[i]);
                 if (edge) {
-                    /* participation flips for a tiny change of p or t^2, or of u */
-                    if (fabs(t0 + Av * dm) < knot_eps * dtg || fabs(rad) < knot_eps * dtg * dtg)
+                    /* participation flips for a tiny change of p = t0 + A dm or of t^2
+                     * (p is exact when A dm = 0, t^2 when every moveout term is 0) */
+                    if ((Av * dm != 0.0 && fabs(t0 + Av * dm) < knot_eps * dtg) ||
+                        (!exact && fabs(rad) < knot_eps * dtg * dtg))
                         flag = 1;
                 }
                 if (!crs_time(t0, Av, Bv, Cv, dm, (double)h[i], dtg, &u, &p, NULL)) continue;
-                if (edge && (dm != 0.0 || h[i] != 0.0f) && edge_sensitive(u, ns_i, hw, knot_eps))
-                    flag = 1;
+                if (edge && !exact && edge_sensitive(u, ns_i, hw, knot_eps)) flag = 1;
                 N += intersect(traces + trace_off[i], ns_i, u, hw, num, &den, &ac);
             }
             const double s = semblance_of(num, w, den, N);

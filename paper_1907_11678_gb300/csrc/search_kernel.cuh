@@ -101,6 +101,24 @@ __device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// a + b rounded toward -infinity (used for the floor below)
+__device__ __forceinline__ f2_t add2_rm(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// floor() by rounding: for |D| < 2^22, D + 1.5*2^23 rounded toward -inf is
+// 1.5*2^23 + floor(D) exactly, so its bit pattern minus that of 1.5*2^23 is floor(D) as an
+// integer and subtracting 1.5*2^23 back gives floor(D) as a float.  Out-of-range or NaN D
+// give huge positive or negative integers, which the range test rejects.
+constexpr float kFloorShift = 12582912.0f;     // 1.5 * 2^23
+constexpr int kFloorShiftBits = 0x4B400000;
 
 __device__ __forceinline__ float warp_min(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
@@ -134,33 +152,55 @@ __device__ __forceinline__ void decode_candidate(const SearchParams& P, int c, f
     }
 }
 
-// One intersection's traveltime -> (window start pointer, fraction, takes part).
+// Two intersections (candidates a, b of one packed pair) with one trace: traveltime ->
+// (window start index in shared memory, interpolation fraction, takes part).  Rows past
+// the owner's end carry n = 2^24 so that their k falls outside every trace.
 template <bool CRS>
-__device__ __forceinline__ void intersect_setup(float A, float B, float C, const TraceMeta& tm,
-                                                int n, float nf, float n2, bool act,
-                                                const float* fb, const float* zeros,
-                                                const float*& p, float& x, bool& ok) {
-    float D;
+__device__ __forceinline__ void intersect_pair(f2_t A2, f2_t B2, f2_t C2, const TraceMeta& tm,
+                                               int n, f2_t nf2, f2_t nsq2, int kb, int zidx,
+                                               int& ia, int& ib, float& xa, float& xb,
+                                               bool& oka, bool& okb) {
+    const f2_t q2 = pk2(tm.q, tm.q);
+    f2_t D2;
+    bool pa_ok = true, pb_ok = true;
     if (CRS) {
-        const float a = A * tm.e;
-        const float pp = nf + a;
-        const float rr = fmaf(B, tm.g, C * tm.q);
-        const float rad = fmaf(pp, pp, rr);
-        const float s = sqrt_fast(rad);
-        D = fmaf(rr, rcp_fast(fmaxf(s + pp, 1e-30f)), a);
-        ok = act && (pp >= 0.f) && (rad >= 0.f);
+        const f2_t a2 = mul2(A2, pk2(tm.e, tm.e));
+        const f2_t pp2 = add2(nf2, a2);
+        const f2_t rr2 = fma2(B2, pk2(tm.g, tm.g), mul2(C2, q2));
+        const f2_t rad2 = fma2(pp2, pp2, rr2);
+        float ra, rb, pa, pb;
+        up2(rad2, ra, rb);
+        up2(pp2, pa, pb);
+        pa_ok = pa >= 0.f;
+        pb_ok = pb >= 0.f;
+        const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), pp2);
+        float sa, sb;
+        up2(sum2, sa, sb);
+        D2 = fma2(rr2, pk2(rcp_fast(fmaxf(sa, 1e-30f)), rcp_fast(fmaxf(sb, 1e-30f))), a2);
     } else {
-        const float cq = C * tm.q;
-        const float rad = n2 + cq;
-        const float s = sqrt_fast(rad);
-        D = cq * rcp_fast(fmaxf(s + nf, 1e-30f));
-        ok = act && (rad >= 0.f);
+        const f2_t cq2 = mul2(C2, q2);
+        const f2_t rad2 = add2(nsq2, cq2);
+        float ra, rb;
+        up2(rad2, ra, rb);
+        const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), nf2);   // nf >= 1e-30
+        float sa, sb;
+        up2(sum2, sa, sb);
+        D2 = mul2(cq2, pk2(rcp_fast(sa), rcp_fast(sb)));
     }
-    const float fl = floorf(D);
-    const int k = n + __float2int_rz(fminf(fl, 16777216.f));
-    ok = ok && (k >= tm.kmin) && (k <= tm.kmax);
-    x = ok ? (D - fl) : 0.f;
-    p = ok ? (fb + k) : zeros;
+    const f2_t shift2 = pk2(kFloorShift, kFloorShift);
+    const f2_t t2 = add2_rm(D2, shift2);
+    const f2_t x2 = sub2(D2, sub2(t2, shift2));
+    float ta, tb;
+    up2(t2, ta, tb);
+    up2(x2, xa, xb);
+    const int ka = n + (__float_as_int(ta) - kFloorShiftBits);
+    const int kb2 = n + (__float_as_int(tb) - kFloorShiftBits);
+    oka = pa_ok && (unsigned)(ka - tm.kmin) <= (unsigned)(tm.kmax - tm.kmin);
+    okb = pb_ok && (unsigned)(kb2 - tm.kmin) <= (unsigned)(tm.kmax - tm.kmin);
+    xa = oka ? xa : 0.f;
+    xb = okb ? xb : 0.f;
+    ia = oka ? kb + ka : zidx;
+    ib = okb ? kb + kb2 : zidx;
 }
 
 template <bool CRS, int W>
@@ -322,20 +362,25 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
     }
 
     // ================================ consumer warps =====================================
-    const int n = n0 + lane;
-    const bool act = n < nrows;
-    const float nf = (float)n;
-    const float n2 = nf * nf;
+    const float* smf = reinterpret_cast<const float*>(smem_raw);
+    const int zidx = (int)(reinterpret_cast<const float*>(sm.zeros) - smf);
+    const bool act = n0 + lane < nrows;
+    const int n = act ? n0 + lane : (1 << 24);        // inactive rows never take part
+    const float nf = fmaxf((float)n, 1e-30f);         // > 0 keeps sqrt(n^2 + Cq) + n > 0
+    const f2_t nf2 = pk2(nf, nf);
+    const f2_t nsq2 = pk2(nf * nf, nf * nf);
     f2_t num[kR / 2][W];
-    f2_t den[kR / 2];
+    f2_t den[kR / 2][2];                              // even / odd window positions
     int cntv[kR];
-    float Ar[kR], Br[kR], Cr[kR];
+    f2_t A2[kR / 2], B2[kR / 2], C2[kR / 2];
     int cidx[kR];
     float bestS = -1.f, bestT = 0.f;
     int bestC = INT_MAX;
     bool aborted = false;
     #pragma unroll
-    for (int r = 0; r < kR; ++r) { cidx[r] = INT_MAX; Ar[r] = Br[r] = Cr[r] = 0.f; cntv[r] = 0; }
+    for (int r = 0; r < kR; ++r) { cidx[r] = INT_MAX; cntv[r] = 0; }
+    #pragma unroll
+    for (int r2 = 0; r2 < kR / 2; ++r2) A2[r2] = B2[r2] = C2[r2] = 0ull;
 
     for (int s = 0;; ++s) {
         const int slot = s % kSlots;
@@ -351,74 +396,79 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
             break;
         }
         if (d.first) {
+            float Ar[kR], Br[kR], Cr[kR];
             #pragma unroll
             for (int r = 0; r < kR; ++r) {
                 const int c = d.pass * kCB + r * kWarps + warp;
                 cidx[r] = c;
-                Ar[r] = Br[r] = Cr[r] = 0.f;
+                Ar[r] = Br[r] = Cr[r] = 0.f;   // past the end: computed, then discarded
                 if (c < P.ncand) decode_candidate<CRS>(P, c, Ar[r], Br[r], Cr[r]);
                 cntv[r] = 0;
             }
             #pragma unroll
             for (int r2 = 0; r2 < kR / 2; ++r2) {
-                den[r2] = 0ull;
+                A2[r2] = pk2(Ar[2 * r2], Ar[2 * r2 + 1]);
+                B2[r2] = pk2(Br[2 * r2], Br[2 * r2 + 1]);
+                C2[r2] = pk2(Cr[2 * r2], Cr[2 * r2 + 1]);
+                den[r2][0] = den[r2][1] = 0ull;
                 #pragma unroll
                 for (int j = 0; j < W; ++j) num[r2][j] = 0ull;
             }
         }
-        const float* sbuf = sm.buf[slot];
         const int ntr = min(d.ntr, kChunkT);
+        const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
         // a pass's second packed pair (r = 2, 3) holds its highest candidates
         const bool pair1 = cidx[2] < P.ncand;
         for (int t = 0; t < ntr; ++t) {
             const TraceMeta tm = sm.meta[slot][t];
-            const float* fb = sbuf + (tm.base - HW);
+            if (tm.kmax < tm.kmin) continue;                 // empty window (warp-uniform)
+            const int kb = slot_base + tm.base - HW;
             #pragma unroll
             for (int r2 = 0; r2 < kR / 2; ++r2) {
                 if (r2 == 1 && !pair1) continue;                      // warp-uniform
-                const int ra = 2 * r2, rb = 2 * r2 + 1;
-                const float* pa;
-                const float* pb;
+                int ia, ib;
                 float xa, xb;
                 bool oka, okb;
-                intersect_setup<CRS>(Ar[ra], Br[ra], Cr[ra], tm, n, nf, n2, act && cidx[ra] < P.ncand,
-                                     fb, sm.zeros, pa, xa, oka);
-                intersect_setup<CRS>(Ar[rb], Br[rb], Cr[rb], tm, n, nf, n2, act && cidx[rb] < P.ncand,
-                                     fb, sm.zeros, pb, xb, okb);
+                intersect_pair<CRS>(A2[r2], B2[r2], C2[r2], tm, n, nf2, nsq2, kb, zidx,
+                                    ia, ib, xa, xb, oka, okb);
                 const f2_t x2 = pk2(xa, xb);
                 f2_t F[W + 1];
                 #pragma unroll
-                for (int j = 0; j <= W; ++j) F[j] = pk2(pa[j], pb[j]);
-                f2_t dd = den[r2];
+                for (int j = 0; j <= W; ++j) F[j] = pk2(smf[ia + j], smf[ib + j]);
                 #pragma unroll
                 for (int j = 0; j < W; ++j) {
                     const f2_t v = fma2(x2, sub2(F[j + 1], F[j]), F[j]);
                     num[r2][j] = add2(num[r2][j], v);
-                    dd = fma2(v, v, dd);
+                    den[r2][j & 1] = fma2(v, v, den[r2][j & 1]);
                 }
-                den[r2] = dd;
-                cntv[ra] += oka ? 1 : 0;
-                cntv[rb] += okb ? 1 : 0;
+                cntv[2 * r2] += oka ? 1 : 0;
+                cntv[2 * r2 + 1] += okb ? 1 : 0;
             }
         }
         if (d.last) {
             #pragma unroll
             for (int r2 = 0; r2 < kR / 2; ++r2) {
-                float nuA = 0.f, nuB = 0.f, acA = 0.f, acB = 0.f, dA, dB;
+                // the numerator is summed in the same even/odd order as the energy, so a
+                // lone participating trace gives exactly S = 1
+                float nuA[2] = {0.f, 0.f}, nuB[2] = {0.f, 0.f}, acA = 0.f, acB = 0.f;
                 #pragma unroll
                 for (int j = 0; j < W; ++j) {
                     float a, b;
                     up2(num[r2][j], a, b);
-                    nuA = fmaf(a, a, nuA); acA += a;
-                    nuB = fmaf(b, b, nuB); acB += b;
+                    nuA[j & 1] = fmaf(a, a, nuA[j & 1]); acA += a;
+                    nuB[j & 1] = fmaf(b, b, nuB[j & 1]); acB += b;
                 }
-                up2(den[r2], dA, dB);
+                float dA0, dB0, dA1, dB1;
+                up2(den[r2][0], dA0, dB0);
+                up2(den[r2][1], dA1, dB1);
+                const float dA = dA0 + dA1, dB = dB0 + dB1;
                 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int r = 2 * r2 + h;
                     const int c = cidx[r];
                     if (c >= P.ncand) continue;
-                    const float nu = h ? nuB : nuA, ac = h ? acB : acA, dn = h ? dB : dA;
+                    const float nu = h ? nuB[0] + nuB[1] : nuA[0] + nuA[1];
+                    const float ac = h ? acB : acA, dn = h ? dB : dA;
                     const float Nf = (float)cntv[r];
                     const float sv = (cntv[r] > 0 && dn > 0.f) ? nu / (Nf * dn) : 0.f;
                     const float st = cntv[r] > 0 ? ac / (Nf * (float)W) : 0.f;
