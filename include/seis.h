@@ -87,6 +87,17 @@ const char* seis_last_error(void);
  * this library recorded a timed-out device wait since the last call (and clears it). */
 int seis_device_status(void* stream);
 
+/* Search kernel variants.  The semblance search kernels come in several tile shapes and
+ * arithmetic forms (consumer warps per CTA, candidates per thread, packed f32x2 or scalar
+ * FP32 accumulation); every variant computes bit-identical results.  The variant used by
+ * cmp_semblance / crs_semblance is a process-wide setting (default 0), normally chosen by
+ * the autotuner (seis_autotune_cmp); changing it while other host threads launch searches
+ * is allowed but those launches may use either value. */
+int seis_search_variant_count(void);
+const char* seis_search_variant_name(int variant);      /* "" if out of range */
+int seis_set_search_variant(int variant);                /* SEIS_EINVAL if out of range */
+int seis_get_search_variant(void);
+
 /* CMP semblance search -- Section 2.1, Eq. 1, Algorithm 1, Section 3.2.
  * For every output row (gather g, t0 = n*dt[g]) and every candidate C[c] (C = 4/v^2,
  * s^2/m^2) each trace of gather g is intersected at t = sqrt(t0^2 + C h^2), its

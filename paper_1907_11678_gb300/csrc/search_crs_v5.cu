@@ -1,0 +1,10 @@
+// search_crs_v5.cu -- CRS instantiations of search kernel variant 5.
+#include "search_kernel.cuh"
+
+namespace seis {
+
+cudaError_t launch_search_crs_v5(const SearchParams& p, int w, cudaStream_t stream) {
+    return launch_search_cfg<true, SearchV5>(p, w, stream);
+}
+
+}  // namespace seis

@@ -35,17 +35,40 @@
 
 namespace seis {
 
-constexpr int kWarps = 7;                    // consumer warps (7 + 1 = 8 warps: 2 CTAs fill
-                                             // the 4 sub-partitions evenly at 128 registers)
-constexpr int kThreads = 32 * (kWarps + 1);  // + one producer warp
-constexpr int kConsumers = 32 * kWarps;
-constexpr int kR = 4;                        // candidates per consumer thread per pass
-constexpr int kCB = kWarps * kR;             // candidates per pass (28 <= producer lanes)
+constexpr int kMaxWarps = 15;                // consumer warps per CTA, at most
 constexpr int kChunkT = 32;                  // traces per stage at most (one per producer lane)
 constexpr int kSlots = 4;                    // ring depth
 constexpr int kBuf = 6144;                   // floats per slot (24 KB)
 constexpr unsigned kFull = 0xffffffffu;
-static_assert(kCB <= 32, "the producer bounds one candidate per lane");
+
+// Arithmetic forms of the window accumulation.  Blackwell's packed f32x2 instructions
+// issue once for two FP32 lanes but run only on the heavy FMA pipe; scalar FP32 runs on
+// either FMA pipe but needs twice the issue slots.  The hybrids split each window
+// sample's work between the two so that neither the issue slots nor the heavy pipe alone
+// bound the kernel.
+enum SearchMode : int {
+    kScalar = 0,    // everything scalar
+    kPacked = 1,    // traveltime and window in f32x2 pairs of candidates
+    kHybridD = 2,   // scalar traveltime and sample difference; packed interpolation and sums
+    kHybridV = 3,   // scalar traveltime, difference and interpolation; packed sums
+};
+
+// Tile shape and arithmetic form of one kernel variant (chosen by the autotuner):
+// NWARP consumer warps + 1 producer warp per CTA, R candidates per consumer thread per
+// pass, accumulation MODE.  Two CTAs per SM.
+template <int NWARP, int R, int MODE>
+struct SearchCfg {
+    static constexpr int kWarps = NWARP;
+    static constexpr int kR = R;
+    static constexpr int kMode = MODE;
+    static constexpr bool kPairs = MODE != kScalar;     // candidates processed in pairs
+    static constexpr int kThreads = 32 * (NWARP + 1);
+    static constexpr int kConsumers = 32 * NWARP;
+    static constexpr int kCB = NWARP * R;     // candidates per pass
+    static_assert(kCB <= 32, "the producer bounds one candidate per lane");
+    static_assert(NWARP <= kMaxWarps, "reduction arrays are sized for kMaxWarps");
+    static_assert(!kPairs || (R % 2) == 0, "candidate pairs need an even R");
+};
 
 struct __align__(16) TraceMeta {
     int base;     // shared-memory float index of sample 0 of the trace in its slot buffer
@@ -70,9 +93,9 @@ struct SearchSmem {
     float zeros[16];
     int abort_flag;
     int pad[3];
-    float redS[kWarps][32];
-    int redC[kWarps][32];
-    float redT[kWarps][32];
+    float redS[kMaxWarps][32];
+    int redC[kMaxWarps][32];
+    float redT[kMaxWarps][32];
 };
 
 // ---- packed FP32 pairs (Blackwell f32x2) -------------------------------------------
@@ -129,8 +152,8 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-__device__ __forceinline__ void consumer_bar() {
-    asm volatile("bar.sync 1, %0;" :: "r"(kConsumers) : "memory");
+__device__ __forceinline__ void consumer_bar(int nthreads) {
+    asm volatile("bar.sync 1, %0;" :: "r"(nthreads) : "memory");
 }
 
 template <bool CRS>
@@ -152,21 +175,66 @@ __device__ __forceinline__ void decode_candidate(const SearchParams& P, int c, f
     }
 }
 
-// Two intersections (candidates a, b of one packed pair) with one trace: traveltime ->
-// (window start index in shared memory, interpolation fraction, takes part).  Rows past
-// the owner's end carry n = 2^24 so that their k falls outside every trace.
+// Per-trace constants of one consumer thread: with kk = k - kmin, the trace takes part iff
+// 0 <= kk <= rng, and its window starts at shared-memory float index kbase + kk.
+struct TraceConst {
+    float q, e, g;
+    int off;        // n - kFloorShiftBits - kmin: kk = bits(D + shift, rounded down) + off
+    unsigned rng;   // kmax - kmin
+    int kbase;      // shared index of the window of k = kmin
+};
+
+__device__ __forceinline__ TraceConst trace_const(const TraceMeta& tm, int n, int slot_base,
+                                                  int hw) {
+    TraceConst c;
+    c.q = tm.q;
+    c.e = tm.e;
+    c.g = tm.g;
+    c.off = n - kFloorShiftBits - tm.kmin;
+    c.rng = (unsigned)(tm.kmax - tm.kmin);
+    c.kbase = slot_base + tm.base - hw + tm.kmin;
+    return c;
+}
+
+// One intersection: traveltime -> (window start index, interpolation fraction, takes part).
+// Rows past the owner's end carry n = 2^24 so that their k falls outside every trace.
 template <bool CRS>
-__device__ __forceinline__ void intersect_pair(f2_t A2, f2_t B2, f2_t C2, const TraceMeta& tm,
-                                               int n, f2_t nf2, f2_t nsq2, int kb, int zidx,
+__device__ __forceinline__ void intersect_one(float A, float B, float C, const TraceConst& tc,
+                                              float nf, float nsq, int zidx,
+                                              int& idx, float& x, bool& ok) {
+    float D;
+    bool p_ok = true;
+    if (CRS) {
+        const float a = A * tc.e;
+        const float pp = nf + a;
+        const float rr = fmaf(B, tc.g, C * tc.q);
+        const float rad = fmaf(pp, pp, rr);
+        p_ok = pp >= 0.f;
+        D = fmaf(rr, rcp_fast(fmaxf(sqrt_fast(rad) + pp, 1e-30f)), a);
+    } else {
+        const float cq = C * tc.q;
+        D = cq * rcp_fast(sqrt_fast(nsq + cq) + nf);            // nf >= 1e-30
+    }
+    const float t = __fadd_rd(D, kFloorShift);
+    const int kk = __float_as_int(t) + tc.off;
+    ok = p_ok && (unsigned)kk <= tc.rng;
+    x = ok ? D - (t - kFloorShift) : 0.f;
+    idx = ok ? tc.kbase + kk : zidx;
+}
+
+// Two intersections (candidates a, b) with the traveltime arithmetic in f32x2 pairs.
+template <bool CRS>
+__device__ __forceinline__ void intersect_pair(f2_t A2, f2_t B2, f2_t C2, const TraceConst& tc,
+                                               f2_t nf2, f2_t nsq2, int zidx,
                                                int& ia, int& ib, float& xa, float& xb,
                                                bool& oka, bool& okb) {
-    const f2_t q2 = pk2(tm.q, tm.q);
+    const f2_t q2 = pk2(tc.q, tc.q);
     f2_t D2;
     bool pa_ok = true, pb_ok = true;
     if (CRS) {
-        const f2_t a2 = mul2(A2, pk2(tm.e, tm.e));
+        const f2_t a2 = mul2(A2, pk2(tc.e, tc.e));
         const f2_t pp2 = add2(nf2, a2);
-        const f2_t rr2 = fma2(B2, pk2(tm.g, tm.g), mul2(C2, q2));
+        const f2_t rr2 = fma2(B2, pk2(tc.g, tc.g), mul2(C2, q2));
         const f2_t rad2 = fma2(pp2, pp2, rr2);
         float ra, rb, pa, pb;
         up2(rad2, ra, rb);
@@ -193,19 +261,23 @@ __device__ __forceinline__ void intersect_pair(f2_t A2, f2_t B2, f2_t C2, const 
     float ta, tb;
     up2(t2, ta, tb);
     up2(x2, xa, xb);
-    const int ka = n + (__float_as_int(ta) - kFloorShiftBits);
-    const int kb2 = n + (__float_as_int(tb) - kFloorShiftBits);
-    oka = pa_ok && (unsigned)(ka - tm.kmin) <= (unsigned)(tm.kmax - tm.kmin);
-    okb = pb_ok && (unsigned)(kb2 - tm.kmin) <= (unsigned)(tm.kmax - tm.kmin);
+    const int kka = __float_as_int(ta) + tc.off;
+    const int kkb = __float_as_int(tb) + tc.off;
+    oka = pa_ok && (unsigned)kka <= tc.rng;
+    okb = pb_ok && (unsigned)kkb <= tc.rng;
     xa = oka ? xa : 0.f;
     xb = okb ? xb : 0.f;
-    ia = oka ? kb + ka : zidx;
-    ib = okb ? kb + kb2 : zidx;
+    ia = oka ? tc.kbase + kka : zidx;
+    ib = okb ? tc.kbase + kkb : zidx;
 }
 
-template <bool CRS, int W>
-__global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams P) {
+template <bool CRS, int W, class CFG>
+__global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchParams P) {
     constexpr int HW = W / 2;
+    constexpr int kWarps = CFG::kWarps;
+    constexpr int kR = CFG::kR;
+    constexpr int kCB = CFG::kCB;
+    constexpr int kConsumers = CFG::kConsumers;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SearchSmem& sm = *reinterpret_cast<SearchSmem*>(smem_raw);
 
@@ -323,19 +395,20 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
             }
             const bool fits = v && (pre <= kBuf);
             int nfit = __popc(__ballot_sync(kFull, fits));    // a prefix of the lanes
+            // traces whose window is empty for this pass are left out of the stage
+            const unsigned present = __ballot_sync(kFull, lane < nfit && n_el > 0);
+            int ntr = __popc(present);
             if (nfit == 0 && M > pl_t) {
                 // a single window larger than a slot (traces are limited on the host so this
                 // cannot happen): drop that trace for this pass and record it
-                if (lane == 0) {
-                    record_status(P.status, kStatusOverflow);
-                    sm.meta[slot][0] = TraceMeta{0, 1, 0, 0.f, 0.f, 0.f, 0, 0};
-                }
+                if (lane == 0) record_status(P.status, kStatusOverflow);
                 nfit = 1;
-            } else if (lane < nfit) {
+                ntr = 0;
+            } else if (lane < nfit && n_el > 0) {
                 const int off = pre - len;                       // multiple of 4 floats
                 tm.base = off + mis - lo;
-                sm.meta[slot][lane] = tm;
-                if (n_el > 0) {
+                sm.meta[slot][__popc(present & ((1u << lane) - 1u))] = tm;
+                {
                     float* dst = slotbuf + off + mis;
                     const int head = min((4 - mis) & 3, n_el);
                     const int nb = (n_el - head) & ~3;
@@ -349,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
             }
             pl_t += nfit;
             const int last = (pl_t >= M);
-            if (lane == 0) sm.desc[slot] = StageDesc{pl_pass, nfit, first, last, 0, 0, 0, 0};
+            if (lane == 0) sm.desc[slot] = StageDesc{pl_pass, ntr, first, last, 0, 0, 0, 0};
             if (last) { ++pl_pass; pl_t = 0; }
             __syncwarp();
             mbar_arrive(&sm.full[slot]);
@@ -368,19 +441,23 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
     const int n = act ? n0 + lane : (1 << 24);        // inactive rows never take part
     const float nf = fmaxf((float)n, 1e-30f);         // > 0 keeps sqrt(n^2 + Cq) + n > 0
     const f2_t nf2 = pk2(nf, nf);
-    const f2_t nsq2 = pk2(nf * nf, nf * nf);
-    f2_t num[kR / 2][W];
-    f2_t den[kR / 2][2];                              // even / odd window positions
+    const float nsq = nf * nf;
+    const f2_t nsq2 = pk2(nsq, nsq);
+    constexpr bool kP = CFG::kPairs;
+    constexpr int kG = kP ? kR / 2 : kR;             // accumulator groups per thread
+    f2_t num2[kP ? kG : 1][W];
+    f2_t den2[kP ? kG : 1][2];                       // even / odd window positions
+    float num1[kP ? 1 : kG][W];
+    float den1[kP ? 1 : kG][2];
     int cntv[kR];
-    f2_t A2[kR / 2], B2[kR / 2], C2[kR / 2];
+    float Ar[kR], Br[kR], Cr[kR];
+    f2_t A2[kP ? kG : 1], B2[kP ? kG : 1], C2[kP ? kG : 1];
     int cidx[kR];
     float bestS = -1.f, bestT = 0.f;
     int bestC = INT_MAX;
     bool aborted = false;
     #pragma unroll
-    for (int r = 0; r < kR; ++r) { cidx[r] = INT_MAX; cntv[r] = 0; }
-    #pragma unroll
-    for (int r2 = 0; r2 < kR / 2; ++r2) A2[r2] = B2[r2] = C2[r2] = 0ull;
+    for (int r = 0; r < kR; ++r) { cidx[r] = INT_MAX; cntv[r] = 0; Ar[r] = Br[r] = Cr[r] = 0.f; }
 
     for (int s = 0;; ++s) {
         const int slot = s % kSlots;
@@ -396,85 +473,139 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
             break;
         }
         if (d.first) {
-            float Ar[kR], Br[kR], Cr[kR];
             #pragma unroll
             for (int r = 0; r < kR; ++r) {
-                const int c = d.pass * kCB + r * kWarps + warp;
+                const int c = d.pass * kCB + warp * kR + r;
                 cidx[r] = c;
                 Ar[r] = Br[r] = Cr[r] = 0.f;   // past the end: computed, then discarded
                 if (c < P.ncand) decode_candidate<CRS>(P, c, Ar[r], Br[r], Cr[r]);
                 cntv[r] = 0;
             }
             #pragma unroll
-            for (int r2 = 0; r2 < kR / 2; ++r2) {
-                A2[r2] = pk2(Ar[2 * r2], Ar[2 * r2 + 1]);
-                B2[r2] = pk2(Br[2 * r2], Br[2 * r2 + 1]);
-                C2[r2] = pk2(Cr[2 * r2], Cr[2 * r2 + 1]);
-                den[r2][0] = den[r2][1] = 0ull;
-                #pragma unroll
-                for (int j = 0; j < W; ++j) num[r2][j] = 0ull;
+            for (int g = 0; g < kG; ++g) {
+                if constexpr (kP) {
+                    A2[g] = pk2(Ar[2 * g], Ar[2 * g + 1]);
+                    B2[g] = pk2(Br[2 * g], Br[2 * g + 1]);
+                    C2[g] = pk2(Cr[2 * g], Cr[2 * g + 1]);
+                    den2[g][0] = den2[g][1] = 0ull;
+                    #pragma unroll
+                    for (int j = 0; j < W; ++j) num2[g][j] = 0ull;
+                } else {
+                    den1[g][0] = den1[g][1] = 0.f;
+                    #pragma unroll
+                    for (int j = 0; j < W; ++j) num1[g][j] = 0.f;
+                }
             }
         }
         const int ntr = min(d.ntr, kChunkT);
         const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
-        // a pass's second packed pair (r = 2, 3) holds its highest candidates
-        const bool pair1 = cidx[2] < P.ncand;
-        for (int t = 0; t < ntr; ++t) {
-            const TraceMeta tm = sm.meta[slot][t];
-            if (tm.kmax < tm.kmin) continue;                 // empty window (warp-uniform)
-            const int kb = slot_base + tm.base - HW;
-            #pragma unroll
-            for (int r2 = 0; r2 < kR / 2; ++r2) {
-                if (r2 == 1 && !pair1) continue;                      // warp-uniform
-                int ia, ib;
-                float xa, xb;
-                bool oka, okb;
-                intersect_pair<CRS>(A2[r2], B2[r2], C2[r2], tm, n, nf2, nsq2, kb, zidx,
-                                    ia, ib, xa, xb, oka, okb);
-                const f2_t x2 = pk2(xa, xb);
-                f2_t F[W + 1];
-                #pragma unroll
-                for (int j = 0; j <= W; ++j) F[j] = pk2(smf[ia + j], smf[ib + j]);
-                #pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    const f2_t v = fma2(x2, sub2(F[j + 1], F[j]), F[j]);
-                    num[r2][j] = add2(num[r2][j], v);
-                    den[r2][j & 1] = fma2(v, v, den[r2][j & 1]);
+        // a warp whose candidates of this pass all lie past the end skips the stage
+        if (ntr > 0 && cidx[0] < P.ncand) {
+            // Software pipeline: the traveltimes of trace t+1 (long MUFU chains) are formed
+            // while the window of trace t is accumulated.
+            int sI[kR];
+            float sX[kR];
+            bool sO[kR];
+            auto setup = [&](int t) {
+                const TraceConst tc = trace_const(sm.meta[slot][t], n, slot_base, HW);
+                if constexpr (CFG::kMode == kPacked) {
+                    #pragma unroll
+                    for (int g = 0; g < kG; ++g)
+                        intersect_pair<CRS>(A2[g], B2[g], C2[g], tc, nf2, nsq2, zidx, sI[2 * g],
+                                            sI[2 * g + 1], sX[2 * g], sX[2 * g + 1], sO[2 * g],
+                                            sO[2 * g + 1]);
+                } else {
+                    #pragma unroll
+                    for (int r = 0; r < kR; ++r)
+                        intersect_one<CRS>(Ar[r], Br[r], Cr[r], tc, nf, nsq, zidx, sI[r], sX[r], sO[r]);
                 }
-                cntv[2 * r2] += oka ? 1 : 0;
-                cntv[2 * r2 + 1] += okb ? 1 : 0;
+            };
+            setup(0);
+            for (int t = 0; t < ntr; ++t) {
+                int cI[kR];
+                float cX[kR];
+                #pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    cI[r] = sI[r];
+                    cX[r] = sX[r];
+                    cntv[r] += sO[r] ? 1 : 0;
+                }
+                setup(min(t + 1, ntr - 1));
+                #pragma unroll
+                for (int g = 0; g < kG; ++g) {
+                    if constexpr (CFG::kMode == kScalar) {
+                        float F[W + 1];
+                        #pragma unroll
+                        for (int j = 0; j <= W; ++j) F[j] = smf[cI[g] + j];
+                        #pragma unroll
+                        for (int j = 0; j < W; ++j) {
+                            const float v = fmaf(cX[g], F[j + 1] - F[j], F[j]);
+                            num1[g][j] += v;
+                            den1[g][j & 1] = fmaf(v, v, den1[g][j & 1]);
+                        }
+                    } else {
+                        const int ra = 2 * g, rb = 2 * g + 1;
+                        float FA[W + 1], FB[W + 1];
+                        #pragma unroll
+                        for (int j = 0; j <= W; ++j) { FA[j] = smf[cI[ra] + j]; FB[j] = smf[cI[rb] + j]; }
+                        const f2_t x2 = pk2(cX[ra], cX[rb]);
+                        #pragma unroll
+                        for (int j = 0; j < W; ++j) {
+                            f2_t v;
+                            if constexpr (CFG::kMode == kPacked) {
+                                v = fma2(x2, sub2(pk2(FA[j + 1], FB[j + 1]), pk2(FA[j], FB[j])),
+                                         pk2(FA[j], FB[j]));
+                            } else if constexpr (CFG::kMode == kHybridD) {
+                                v = fma2(x2, pk2(FA[j + 1] - FA[j], FB[j + 1] - FB[j]),
+                                         pk2(FA[j], FB[j]));
+                            } else {
+                                v = pk2(fmaf(cX[ra], FA[j + 1] - FA[j], FA[j]),
+                                        fmaf(cX[rb], FB[j + 1] - FB[j], FB[j]));
+                            }
+                            num2[g][j] = add2(num2[g][j], v);
+                            den2[g][j & 1] = fma2(v, v, den2[g][j & 1]);
+                        }
+                    }
+                }
             }
         }
         if (d.last) {
             #pragma unroll
-            for (int r2 = 0; r2 < kR / 2; ++r2) {
+            for (int r = 0; r < kR; ++r) {
+                const int c = cidx[r];
+                if (c >= P.ncand) continue;
                 // the numerator is summed in the same even/odd order as the energy, so a
                 // lone participating trace gives exactly S = 1
-                float nuA[2] = {0.f, 0.f}, nuB[2] = {0.f, 0.f}, acA = 0.f, acB = 0.f;
+                float nu0 = 0.f, nu1 = 0.f, ac = 0.f, d0, d1;
                 #pragma unroll
                 for (int j = 0; j < W; ++j) {
-                    float a, b;
-                    up2(num[r2][j], a, b);
-                    nuA[j & 1] = fmaf(a, a, nuA[j & 1]); acA += a;
-                    nuB[j & 1] = fmaf(b, b, nuB[j & 1]); acB += b;
+                    float a;
+                    if constexpr (kP) {
+                        float lo, hi;
+                        up2(num2[r / 2][j], lo, hi);
+                        a = (r & 1) ? hi : lo;
+                    } else {
+                        a = num1[r][j];
+                    }
+                    if (j & 1) nu1 = fmaf(a, a, nu1); else nu0 = fmaf(a, a, nu0);
+                    ac += a;
                 }
-                float dA0, dB0, dA1, dB1;
-                up2(den[r2][0], dA0, dB0);
-                up2(den[r2][1], dA1, dB1);
-                const float dA = dA0 + dA1, dB = dB0 + dB1;
-                #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int r = 2 * r2 + h;
-                    const int c = cidx[r];
-                    if (c >= P.ncand) continue;
-                    const float nu = h ? nuB[0] + nuB[1] : nuA[0] + nuA[1];
-                    const float ac = h ? acB : acA, dn = h ? dB : dA;
-                    const float Nf = (float)cntv[r];
-                    const float sv = (cntv[r] > 0 && dn > 0.f) ? nu / (Nf * dn) : 0.f;
-                    const float st = cntv[r] > 0 ? ac / (Nf * (float)W) : 0.f;
-                    if (P.S_cube && act) P.S_cube[(row0 + n) * (int64_t)P.ncand + c] = sv;
-                    if (sv > bestS) { bestS = sv; bestC = c; bestT = st; }
+                if constexpr (kP) {
+                    float l0, h0, l1, h1;
+                    up2(den2[r / 2][0], l0, h0);
+                    up2(den2[r / 2][1], l1, h1);
+                    d0 = (r & 1) ? h0 : l0;
+                    d1 = (r & 1) ? h1 : l1;
+                } else {
+                    d0 = den1[r][0];
+                    d1 = den1[r][1];
                 }
+                const float nu = nu0 + nu1, dn = d0 + d1;
+                const float Nf = (float)cntv[r];
+                const float sv = (cntv[r] > 0 && dn > 0.f) ? nu / (Nf * dn) : 0.f;
+                const float st = cntv[r] > 0 ? ac / (Nf * (float)W) : 0.f;
+                if (P.S_cube && act) P.S_cube[(row0 + n) * (int64_t)P.ncand + c] = sv;
+                if (sv > bestS) { bestS = sv; bestC = c; bestT = st; }
             }
         }
         mbar_arrive(&sm.empty[slot]);                   // this thread is done with the slot
@@ -483,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
     sm.redS[warp][lane] = bestS;
     sm.redC[warp][lane] = bestC;
     sm.redT[warp][lane] = bestT;
-    consumer_bar();
+    consumer_bar(kConsumers);
     if (aborted || sm.abort_flag) return;
     if (warp == 0 && act) {
         float bs = sm.redS[0][lane], bt = sm.redT[0][lane];
@@ -513,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const SearchParams 
     }
 }
 
-template <bool CRS, int W>
+template <bool CRS, int W, class CFG>
 cudaError_t launch_search_w(const SearchParams& p, cudaStream_t stream) {
     static bool configured[64] = {};  // dynamic shared-memory opt-in, once per device
     const int smem = (int)sizeof(SearchSmem);
@@ -521,31 +652,44 @@ cudaError_t launch_search_w(const SearchParams& p, cudaStream_t stream) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(search_kernel<CRS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem);
+        e = cudaFuncSetAttribute(search_kernel<CRS, W, CFG>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
     const int64_t grid = p.nowner * (int64_t)p.tiles_per_owner;
     if (grid <= 0) return cudaSuccess;
     if (grid > INT_MAX) return cudaErrorInvalidValue;
-    search_kernel<CRS, W><<<(unsigned)grid, kThreads, smem, stream>>>(p);
+    search_kernel<CRS, W, CFG><<<(unsigned)grid, CFG::kThreads, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
-template <bool CRS>
-cudaError_t launch_search_dispatch(const SearchParams& p, int w, cudaStream_t stream) {
+template <bool CRS, class CFG>
+cudaError_t launch_search_cfg(const SearchParams& p, int w, cudaStream_t stream) {
     switch (w) {
-        case 1: return launch_search_w<CRS, 1>(p, stream);
-        case 3: return launch_search_w<CRS, 3>(p, stream);
-        case 5: return launch_search_w<CRS, 5>(p, stream);
-        case 7: return launch_search_w<CRS, 7>(p, stream);
-        case 9: return launch_search_w<CRS, 9>(p, stream);
-        case 11: return launch_search_w<CRS, 11>(p, stream);
-        case 13: return launch_search_w<CRS, 13>(p, stream);
-        case 15: return launch_search_w<CRS, 15>(p, stream);
+        case 1: return launch_search_w<CRS, 1, CFG>(p, stream);
+        case 3: return launch_search_w<CRS, 3, CFG>(p, stream);
+        case 5: return launch_search_w<CRS, 5, CFG>(p, stream);
+        case 7: return launch_search_w<CRS, 7, CFG>(p, stream);
+        case 9: return launch_search_w<CRS, 9, CFG>(p, stream);
+        case 11: return launch_search_w<CRS, 11, CFG>(p, stream);
+        case 13: return launch_search_w<CRS, 13, CFG>(p, stream);
+        case 15: return launch_search_w<CRS, 15, CFG>(p, stream);
         default: return cudaErrorInvalidValue;
     }
 }
+
+// The kernel variants the autotuner chooses from (index = variant id).
+using SearchV0 = SearchCfg<7, 4, kPacked>;
+using SearchV1 = SearchCfg<7, 4, kScalar>;
+using SearchV2 = SearchCfg<11, 2, kHybridD>;
+using SearchV3 = SearchCfg<11, 2, kScalar>;
+using SearchV4 = SearchCfg<15, 2, kPacked>;
+using SearchV5 = SearchCfg<15, 2, kScalar>;
+using SearchV6 = SearchCfg<11, 2, kHybridV>;
+using SearchV7 = SearchCfg<15, 2, kHybridV>;
+using SearchV8 = SearchCfg<7, 4, kHybridD>;
+using SearchV9 = SearchCfg<7, 4, kHybridV>;
+constexpr int kSearchVariants = 10;
 
 }  // namespace seis

@@ -1,6 +1,7 @@
 // seis_api.cu -- the C ABI of libseis (declared in include/seis.h): argument checks,
 // error reporting, the device status word, and the CRS aperture build.
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -56,11 +57,26 @@ static int check_w(int32_t w) {
     return SEIS_OK;
 }
 
+static std::atomic<int> g_variant{0};
+
 }  // namespace seis
 
 using namespace seis;
 
 extern "C" const char* seis_last_error(void) { return g_err; }
+
+extern "C" int seis_search_variant_count(void) { return search_variant_count(); }
+
+extern "C" const char* seis_search_variant_name(int variant) { return search_variant_name(variant); }
+
+extern "C" int seis_set_search_variant(int variant) {
+    if (variant < 0 || variant >= search_variant_count())
+        return fail(SEIS_EINVAL, "variant %d outside [0, %d)", variant, search_variant_count());
+    g_variant.store(variant);
+    return SEIS_OK;
+}
+
+extern "C" int seis_get_search_variant(void) { return g_variant.load(); }
 
 extern "C" int seis_device_status(void* stream) {
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
@@ -108,6 +124,7 @@ extern "C" int cmp_semblance(const seis_gathers* d, const float* C, int32_t nc, 
     p.best_S = best_S;
     p.stack = stack_out;
     p.status = device_status_word();
+    p.variant = g_variant.load();
     cudaError_t e = launch_search(p, false, w, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "cmp_semblance launch");
     return SEIS_OK;
@@ -154,6 +171,7 @@ extern "C" int crs_semblance(const seis_gathers* d, const seis_aperture* ap, con
     p.best_S = best_S;
     p.stack = stack_out;
     p.status = device_status_word();
+    p.variant = g_variant.load();
     cudaError_t e = launch_search(p, true, w, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "crs_semblance launch");
     return SEIS_OK;

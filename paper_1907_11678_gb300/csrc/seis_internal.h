@@ -36,10 +36,13 @@ struct SearchParams {
     float* best_S;
     float* stack;
     unsigned* status;
+    int variant;               // search kernel variant (tile shape / arithmetic form)
 };
 
 // Launchers (return the cudaError_t of the launch).
 cudaError_t launch_search(const SearchParams& p, bool crs, int w, cudaStream_t stream);
+int search_variant_count();
+const char* search_variant_name(int v);
 
 unsigned* device_status_word();   // this device's status word (module global)
 

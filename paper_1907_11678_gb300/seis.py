@@ -68,8 +68,12 @@ def load_library(path: str | None = None):
                                           vp, vp, vp, vp, vp, vp]
             lib.seis_crs_aperture.argtypes = [vp, vp, i64, f32, vp, vp, i64, vp, vp, vp,
                                               vp, vp, vp, vp]
+            lib.seis_search_variant_name.restype = ctypes.c_char_p
+            lib.seis_search_variant_name.argtypes = [ctypes.c_int]
+            lib.seis_set_search_variant.argtypes = [ctypes.c_int]
             for name in ("seis_device_status", "cmp_semblance", "crs_semblance",
-                         "seis_crs_aperture"):
+                         "seis_crs_aperture", "seis_search_variant_count",
+                         "seis_set_search_variant", "seis_get_search_variant"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -233,6 +237,20 @@ def crs_semblance(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor, C:
                            _ptr(out["stack"]), _stream_handle(stream))
     _check(rc)
     return out
+
+
+def search_variants() -> list[str]:
+    """Names of the search kernel variants (index = variant id)."""
+    lib = load_library()
+    return [lib.seis_search_variant_name(i).decode() for i in range(lib.seis_search_variant_count())]
+
+
+def set_search_variant(v: int) -> None:
+    _check(load_library().seis_set_search_variant(int(v)))
+
+
+def get_search_variant() -> int:
+    return int(load_library().seis_get_search_variant())
 
 
 def device_status(stream=None) -> None:
