@@ -88,15 +88,36 @@ const char* seis_last_error(void);
 int seis_device_status(void* stream);
 
 /* Search kernel variants.  The semblance search kernels come in several tile shapes and
- * arithmetic forms (consumer warps per CTA, candidates per thread, packed f32x2 or scalar
- * FP32 accumulation); every variant computes bit-identical results.  The variant used by
- * cmp_semblance / crs_semblance is a process-wide setting (default 0), normally chosen by
- * the autotuner (seis_autotune_cmp); changing it while other host threads launch searches
- * is allowed but those launches may use either value. */
+ * arithmetic forms (consumer warps per CTA, candidates per thread, scalar / packed f32x2 /
+ * hybrid FP32 accumulation); every variant computes bit-identical results.  A launch uses
+ * the variant the autotuner recorded for its shape bucket (kind, w, and log2 buckets of
+ * the candidate count, rows per owner and traces per gather), else the process-wide
+ * default set here (initially 5).  Changing it while other host threads launch searches is
+ * allowed; those launches use either value. */
 int seis_search_variant_count(void);
 const char* seis_search_variant_name(int variant);      /* "" if out of range */
 int seis_set_search_variant(int variant);                /* SEIS_EINVAL if out of range */
 int seis_get_search_variant(void);
+
+/* Autotuner (no counterpart in the paper; it picks the tile shape the paper fixes by hand
+ * for the Sunway LDM, Section 3.3.2 "tile_size").  SYNCHRONOUS: runs every variant once
+ * untimed and `reps` times between CUDA events on `stream`, records the fastest for the
+ * problem's shape bucket and returns it in *chosen (host, may be NULL); ms_out (host,
+ * seis_search_variant_count() floats, may be NULL) receives each variant's mean time.
+ * best_idx / best_S / stack_out are scratch outputs of the problem's size (overwritten).
+ * Arguments as cmp_semblance / crs_semblance; errors likewise. */
+int seis_autotune_cmp(const seis_gathers* d, const float* C, int32_t nc, int32_t w,
+                      int32_t* best_idx, float* best_S, float* stack_out, int32_t reps,
+                      int32_t* chosen, float* ms_out, void* stream);
+int seis_autotune_crs(const seis_gathers* d, const seis_aperture* ap,
+                      const float* A, int32_t nA, const float* B, int32_t nB,
+                      const float* C, int32_t nC, int32_t w,
+                      int32_t* best_idx, float* best_S, float* stack_out, int32_t reps,
+                      int32_t* chosen, float* ms_out, void* stream);
+/* The recorded choices as a JSON file (host path); load merges into the current table. */
+int seis_autotune_save(const char* path);
+int seis_autotune_load(const char* path);
+int seis_autotune_clear(void);
 
 /* CMP semblance search -- Section 2.1, Eq. 1, Algorithm 1, Section 3.2.
  * For every output row (gather g, t0 = n*dt[g]) and every candidate C[c] (C = 4/v^2,
@@ -145,6 +166,37 @@ int crs_semblance(const seis_gathers* d, const seis_aperture* ap,
                   const float* C, int32_t nC, int32_t w,
                   float* S_cube, int32_t* best_idx, float* best_ABC, float* best_S,
                   float* stack_out, void* stream);
+
+/* Stack along given operators -- Algorithm 1's linear accumulator (stack = sum of the
+ * interpolated window samples / (N w)), Section 2.1 (NMO correction and stacking).
+ * ap == NULL: CMP mode, params [rows] = C per output row of the gathers in d.
+ * ap != NULL: CRS mode, params [rows][3] = (A, B, C) per output row of the apertures.
+ *   stack_out [rows]; S_out [rows] semblance at the operator (or NULL); N_out [rows] number
+ *   of traces taking part (or NULL).  Errors: SEIS_EINVAL, SEIS_ECUDA. */
+int stack(const seis_gathers* d, const seis_aperture* ap, const float* params, int32_t w,
+          float* stack_out, float* S_out, int32_t* N_out, void* stream);
+
+/* Adjoint of the CRS semblance (no counterpart in the paper: the derivative of Eq. 1
+ * through the CRS traveltime of Section 2.2 and the linear interpolation of Algorithm 1,
+ * with k and the participation mask held fixed).  For ABC [rows][3] gives S_out [rows],
+ * grad_out [rows][3] = dS/d(A,B,C) and, if non-NULL, stack_out [rows]. */
+int crs_semblance_grad(const seis_gathers* d, const seis_aperture* ap, const float* ABC,
+                       int32_t w, float* S_out, float* grad_out, float* stack_out, void* stream);
+
+/* Gradient-ascent refinement of the CRS operators (no counterpart in the paper; it replaces
+ * the dense 3-D grid search of Section 2.2 by a local search from a coarse pick).  Per row,
+ * in normalised coordinates z = (theta - lo3) / (hi3 - lo3): starting from ABC_inout, `steps`
+ * trials z' = clamp(z + s g/|g|, 0, 1) with g = dS/dz; a trial is accepted when its S is
+ * not lower, otherwise s halves (s starts at step0).  On return ABC_inout holds the accepted
+ * operators and S_out, grad_out [rows][3], stack_out their semblance, gradient and stack.
+ * lo3, hi3: HOST arrays of 3 floats.  rows = ap->out_off[n_central] (host).  workspace:
+ * device scratch of seis_refine_workspace_size(rows) bytes, 256-byte aligned, owned by the
+ * caller.  Asynchronous (1 + 2*steps launches on stream).  Errors: SEIS_EINVAL, SEIS_ECUDA. */
+size_t seis_refine_workspace_size(int64_t rows);
+int crs_refine(const seis_gathers* d, const seis_aperture* ap, float* ABC_inout,
+               const float* lo3, const float* hi3, int32_t steps, float step0, int32_t w,
+               float* S_out, float* grad_out, float* stack_out,
+               void* workspace, size_t ws_bytes, int64_t rows, void* stream);
 
 #ifdef __cplusplus
 }

@@ -271,6 +271,107 @@ __device__ __forceinline__ void intersect_pair(f2_t A2, f2_t B2, f2_t C2, const 
     ib = okb ? tc.kbase + kkb : zidx;
 }
 
+// Window bounds of one stage: the extreme candidate parameters of the rows it serves.
+struct StageBounds {
+    float A0, A1, B0, B1, C0, C1;
+};
+
+// Producer warp, one stage: lane l takes trace pl_t + l of the owner's list, computes the
+// sample window that rows n0..n_last x candidates within `b` can touch (traveltime bounds at
+// the box corners, +-2 samples of margin), and the lanes whose windows fit the slot (a
+// prefix) copy them: one cp.async.bulk of the 16-byte-aligned body plus scalar loads of at
+// most 3 head and 3 tail samples.  Empty windows are left out; the metadata of the others is
+// compacted into meta[0..ntr).  Returns ntr; nfit = traces consumed from the list.
+template <bool CRS, int HW>
+__device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, uint64_t* full,
+                                             const float* traces, const int64_t* trace_off,
+                                             const float* hh, const float* mm, const int32_t* list,
+                                             int64_t lbeg, int M, int pl_t, float dt, float mc,
+                                             int n0, int n_last, const StageBounds& b,
+                                             unsigned* status, int& nfit_out) {
+    const int lane = threadIdx.x & 31;
+    const float bA0 = b.A0, bA1 = b.A1, bB0 = b.B0, bB1 = b.B1, bC0 = b.C0, bC1 = b.C1;
+    fence_proxy_async_smem();   // earlier generic accesses of the slot before async writes
+    const int t = pl_t + lane;
+    const bool v = t < M;
+    int len = 0, n_el = 0, mis = 0, lo = 0;
+    const float* src = nullptr;
+    TraceMeta tm{0, 1, 0, 0.f, 0.f, 0.f, 0, 0};
+    if (v) {
+        const int64_t tid = list ? (int64_t)list[lbeg + t] : (lbeg + t);
+        const int64_t toff = trace_off[tid];
+        const int64_t ns64 = trace_off[tid + 1] - toff;
+        const int ns_i = ns64 < 0 ? 0 : (ns64 > (INT_MAX / 4) ? (INT_MAX / 4) : (int)ns64);
+        const double dtd = (double)dt;
+        const double hd = (double)hh[tid];
+        tm.q = (float)(hd * hd / (dtd * dtd));
+        float aLo = 0.f, aHi = 0.f, rLo, rHi;
+        if (CRS) {
+            const double dm = (double)mm[tid] - (double)mc;
+            tm.e = (float)(dm / dtd);
+            tm.g = (float)(dm * dm / (dtd * dtd));
+            aLo = fminf(bA0 * tm.e, bA1 * tm.e);
+            aHi = fmaxf(bA0 * tm.e, bA1 * tm.e);
+            rLo = bB0 * tm.g + bC0 * tm.q;
+            rHi = bB1 * tm.g + bC1 * tm.q;
+        } else {
+            rLo = bC0 * tm.q;
+            rHi = bC1 * tm.q;
+        }
+        const float pLo = fmaxf((float)n0 + aLo, 0.f);
+        const float pHi = (float)n_last + aHi;
+        const float radLo = pLo * pLo + rLo;
+        const float radHi = pHi * pHi + rHi;
+        if (pHi >= 0.f && radHi >= 0.f) {
+            const float uLo = fminf(sqrtf(fmaxf(radLo, 0.f)), 1.6e7f);
+            const float uHi = fminf(sqrtf(radHi), 1.6e7f);
+            const int kmin = max((int)floorf(uLo) - 2, HW);
+            const int kmax = min((int)floorf(uHi) + 2, ns_i - HW - 2);
+            if (kmin <= kmax) {
+                tm.kmin = kmin;
+                tm.kmax = kmax;
+                lo = kmin - HW;
+                n_el = (kmax + HW + 1) - lo + 1;
+                src = traces + toff + lo;
+                mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+                len = (mis + n_el + 3) & ~3;
+            }
+        }
+    }
+    int pre = len;                                     // inclusive scan of lengths
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, pre, o);
+        if (lane >= o) pre += y;
+    }
+    const bool fits = v && (pre <= kBuf);
+    int nfit = __popc(__ballot_sync(kFull, fits));    // a prefix of the lanes
+    // traces whose window is empty for this stage are left out of it
+    const unsigned present = __ballot_sync(kFull, lane < nfit && n_el > 0);
+    int ntr = __popc(present);
+    if (nfit == 0 && M > pl_t) {
+        // a single window larger than a slot (traces are limited on the host so this
+        // cannot happen): drop that trace and record it
+        if (lane == 0) record_status(status, kStatusOverflow);
+        nfit = 1;
+        ntr = 0;
+    } else if (lane < nfit && n_el > 0) {
+        const int off = pre - len;                       // multiple of 4 floats
+        tm.base = off + mis - lo;
+        meta[__popc(present & ((1u << lane) - 1u))] = tm;
+        float* dst = slotbuf + off + mis;
+        const int head = min((4 - mis) & 3, n_el);
+        const int nb = (n_el - head) & ~3;
+        if (nb > 0) {
+            mbar_expect_tx(full, (uint32_t)nb * 4u);
+            bulk_g2s(dst + head, src + head, (uint32_t)nb * 4u, full);
+        }
+        for (int e2 = 0; e2 < head; ++e2) dst[e2] = ldg_nc(src + e2);
+        for (int e2 = head + nb; e2 < n_el; ++e2) dst[e2] = ldg_nc(src + e2);
+    }
+    nfit_out = nfit;
+    return ntr;
+}
+
 template <bool CRS, int W, class CFG>
 __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchParams P) {
     constexpr int HW = W / 2;
@@ -339,87 +440,12 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
                 bC0 = warp_min(v ? cc : FLT_MAX); bC1 = warp_max(v ? cc : -FLT_MAX);
                 pl_bpass = pl_pass;
             }
-            float* slotbuf = sm.buf[slot];
             const int first = (pl_t == 0);
-            fence_proxy_async_smem();   // earlier generic accesses of the slot before async writes
-            const int t = pl_t + lane;
-            const bool v = t < M;
-            int len = 0, n_el = 0, mis = 0, lo = 0;
-            const float* src = nullptr;
-            TraceMeta tm{0, 1, 0, 0.f, 0.f, 0.f, 0, 0};
-            if (v) {
-                const int64_t tid = P.list ? (int64_t)P.list[lbeg + t] : (lbeg + t);
-                const int64_t toff = P.trace_off[tid];
-                const int64_t ns64 = P.trace_off[tid + 1] - toff;
-                const int ns_i = ns64 < 0 ? 0 : (ns64 > (INT_MAX / 4) ? (INT_MAX / 4) : (int)ns64);
-                const double dtd = (double)dt;
-                const double hd = (double)P.h[tid];
-                tm.q = (float)(hd * hd / (dtd * dtd));
-                float aLo = 0.f, aHi = 0.f, rLo, rHi;
-                if (CRS) {
-                    const double dm = (double)P.m[tid] - (double)mc;
-                    tm.e = (float)(dm / dtd);
-                    tm.g = (float)(dm * dm / (dtd * dtd));
-                    aLo = fminf(bA0 * tm.e, bA1 * tm.e);
-                    aHi = fmaxf(bA0 * tm.e, bA1 * tm.e);
-                    rLo = bB0 * tm.g + bC0 * tm.q;
-                    rHi = bB1 * tm.g + bC1 * tm.q;
-                } else {
-                    rLo = bC0 * tm.q;
-                    rHi = bC1 * tm.q;
-                }
-                const float pLo = fmaxf((float)n0 + aLo, 0.f);
-                const float pHi = (float)n_last + aHi;
-                const float radLo = pLo * pLo + rLo;
-                const float radHi = pHi * pHi + rHi;
-                if (pHi >= 0.f && radHi >= 0.f) {
-                    const float uLo = fminf(sqrtf(fmaxf(radLo, 0.f)), 1.6e7f);
-                    const float uHi = fminf(sqrtf(radHi), 1.6e7f);
-                    const int kmin = max((int)floorf(uLo) - 2, HW);
-                    const int kmax = min((int)floorf(uHi) + 2, ns_i - HW - 2);
-                    if (kmin <= kmax) {
-                        tm.kmin = kmin;
-                        tm.kmax = kmax;
-                        lo = kmin - HW;
-                        n_el = (kmax + HW + 1) - lo + 1;
-                        src = P.traces + toff + lo;
-                        mis = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
-                        len = (mis + n_el + 3) & ~3;
-                    }
-                }
-            }
-            int pre = len;                                     // inclusive scan of lengths
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, pre, o);
-                if (lane >= o) pre += y;
-            }
-            const bool fits = v && (pre <= kBuf);
-            int nfit = __popc(__ballot_sync(kFull, fits));    // a prefix of the lanes
-            // traces whose window is empty for this pass are left out of the stage
-            const unsigned present = __ballot_sync(kFull, lane < nfit && n_el > 0);
-            int ntr = __popc(present);
-            if (nfit == 0 && M > pl_t) {
-                // a single window larger than a slot (traces are limited on the host so this
-                // cannot happen): drop that trace for this pass and record it
-                if (lane == 0) record_status(P.status, kStatusOverflow);
-                nfit = 1;
-                ntr = 0;
-            } else if (lane < nfit && n_el > 0) {
-                const int off = pre - len;                       // multiple of 4 floats
-                tm.base = off + mis - lo;
-                sm.meta[slot][__popc(present & ((1u << lane) - 1u))] = tm;
-                {
-                    float* dst = slotbuf + off + mis;
-                    const int head = min((4 - mis) & 3, n_el);
-                    const int nb = (n_el - head) & ~3;
-                    if (nb > 0) {
-                        mbar_expect_tx(&sm.full[slot], (uint32_t)nb * 4u);
-                        bulk_g2s(dst + head, src + head, (uint32_t)nb * 4u, &sm.full[slot]);
-                    }
-                    for (int e2 = 0; e2 < head; ++e2) dst[e2] = ldg_nc(src + e2);
-                    for (int e2 = head + nb; e2 < n_el; ++e2) dst[e2] = ldg_nc(src + e2);
-                }
-            }
+            int nfit = 0;
+            const int ntr = produce_stage<CRS, HW>(
+                sm.buf[slot], sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h, P.m,
+                P.list, lbeg, M, pl_t, dt, mc, n0, n_last,
+                StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit);
             pl_t += nfit;
             const int last = (pl_t >= M);
             if (lane == 0) sm.desc[slot] = StageDesc{pl_pass, ntr, first, last, 0, 0, 0, 0};

@@ -14,7 +14,7 @@ namespace seis {
 // ------------------------------------------------------------------ error reporting --
 static thread_local char g_err[512] = "";
 
-static int fail(int code, const char* fmt, ...) {
+int fail(int code, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
@@ -22,7 +22,7 @@ static int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-static int cuda_fail(cudaError_t e, const char* where) {
+int cuda_fail(cudaError_t e, const char* where) {
     return fail(SEIS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
@@ -57,43 +57,13 @@ static int check_w(int32_t w) {
     return SEIS_OK;
 }
 
-static std::atomic<int> g_variant{0};
+static std::atomic<int> g_variant{5};
 
-}  // namespace seis
+int default_variant() { return g_variant.load(); }
 
-using namespace seis;
-
-extern "C" const char* seis_last_error(void) { return g_err; }
-
-extern "C" int seis_search_variant_count(void) { return search_variant_count(); }
-
-extern "C" const char* seis_search_variant_name(int variant) { return search_variant_name(variant); }
-
-extern "C" int seis_set_search_variant(int variant) {
-    if (variant < 0 || variant >= search_variant_count())
-        return fail(SEIS_EINVAL, "variant %d outside [0, %d)", variant, search_variant_count());
-    g_variant.store(variant);
-    return SEIS_OK;
-}
-
-extern "C" int seis_get_search_variant(void) { return g_variant.load(); }
-
-extern "C" int seis_device_status(void* stream) {
-    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "seis_device_status");
-    unsigned v = 0, zero = 0;
-    e = cudaMemcpyFromSymbol(&v, g_status, sizeof(v));
-    if (e != cudaSuccess) return cuda_fail(e, "seis_device_status");
-    e = cudaMemcpyToSymbol(g_status, &zero, sizeof(zero));
-    if (e != cudaSuccess) return cuda_fail(e, "seis_device_status");
-    if (v & kStatusTimeout) return fail(SEIS_ETIMEOUT, "a device wait timed out");
-    if (v & kStatusOverflow) return fail(SEIS_EUNSUPPORTED, "a staged trace window overflowed");
-    return SEIS_OK;
-}
-
-extern "C" int cmp_semblance(const seis_gathers* d, const float* C, int32_t nc, int32_t w,
-                             float* S_cube, int32_t* best_idx, float* best_C, float* best_S,
-                             float* stack_out, void* stream) {
+int build_cmp_params(const seis_gathers* d, const float* C, int32_t nc, int32_t w, float* S_cube,
+                     int32_t* best_idx, float* best_C, float* best_S, float* stack_out,
+                     SearchParams* out, TuneKey* key) {
     int rc = check_gathers(d, false);
     if (rc) return rc;
     if ((rc = check_w(w))) return rc;
@@ -124,16 +94,16 @@ extern "C" int cmp_semblance(const seis_gathers* d, const float* C, int32_t nc, 
     p.best_S = best_S;
     p.stack = stack_out;
     p.status = device_status_word();
-    p.variant = g_variant.load();
-    cudaError_t e = launch_search(p, false, w, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "cmp_semblance launch");
+    *key = make_tune_key(false, w, nc, d->max_rows, d->ntraces / d->ngathers);
+    p.variant = lookup_variant(*key, default_variant());
+    *out = p;
     return SEIS_OK;
 }
 
-extern "C" int crs_semblance(const seis_gathers* d, const seis_aperture* ap, const float* A,
-                             int32_t nA, const float* B, int32_t nB, const float* C, int32_t nC,
-                             int32_t w, float* S_cube, int32_t* best_idx, float* best_ABC,
-                             float* best_S, float* stack_out, void* stream) {
+int build_crs_params(const seis_gathers* d, const seis_aperture* ap, const float* A, int32_t nA,
+                     const float* B, int32_t nB, const float* C, int32_t nC, int32_t w,
+                     float* S_cube, int32_t* best_idx, float* best_ABC, float* best_S,
+                     float* stack_out, SearchParams* out, TuneKey* key) {
     int rc = check_gathers(d, true);
     if (rc) return rc;
     if ((rc = check_w(w))) return rc;
@@ -171,7 +141,65 @@ extern "C" int crs_semblance(const seis_gathers* d, const seis_aperture* ap, con
     p.best_S = best_S;
     p.stack = stack_out;
     p.status = device_status_word();
-    p.variant = g_variant.load();
+    *key = make_tune_key(true, w, (int)ncand, ap->max_rows, 0);
+    p.variant = lookup_variant(*key, default_variant());
+    *out = p;
+    return SEIS_OK;
+}
+
+}  // namespace seis
+
+using namespace seis;
+
+extern "C" const char* seis_last_error(void) { return g_err; }
+
+extern "C" int seis_search_variant_count(void) { return search_variant_count(); }
+
+extern "C" const char* seis_search_variant_name(int variant) { return search_variant_name(variant); }
+
+extern "C" int seis_set_search_variant(int variant) {
+    if (variant < 0 || variant >= search_variant_count())
+        return fail(SEIS_EINVAL, "variant %d outside [0, %d)", variant, search_variant_count());
+    g_variant.store(variant);
+    return SEIS_OK;
+}
+
+extern "C" int seis_get_search_variant(void) { return g_variant.load(); }
+
+extern "C" int seis_device_status(void* stream) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "seis_device_status");
+    unsigned v = 0, zero = 0;
+    e = cudaMemcpyFromSymbol(&v, g_status, sizeof(v));
+    if (e != cudaSuccess) return cuda_fail(e, "seis_device_status");
+    e = cudaMemcpyToSymbol(g_status, &zero, sizeof(zero));
+    if (e != cudaSuccess) return cuda_fail(e, "seis_device_status");
+    if (v & kStatusTimeout) return fail(SEIS_ETIMEOUT, "a device wait timed out");
+    if (v & kStatusOverflow) return fail(SEIS_EUNSUPPORTED, "a staged trace window overflowed");
+    return SEIS_OK;
+}
+
+extern "C" int cmp_semblance(const seis_gathers* d, const float* C, int32_t nc, int32_t w,
+                             float* S_cube, int32_t* best_idx, float* best_C, float* best_S,
+                             float* stack_out, void* stream) {
+    SearchParams p;
+    TuneKey key;
+    int rc = build_cmp_params(d, C, nc, w, S_cube, best_idx, best_C, best_S, stack_out, &p, &key);
+    if (rc) return rc;
+    cudaError_t e = launch_search(p, false, w, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cmp_semblance launch");
+    return SEIS_OK;
+}
+
+extern "C" int crs_semblance(const seis_gathers* d, const seis_aperture* ap, const float* A,
+                             int32_t nA, const float* B, int32_t nB, const float* C, int32_t nC,
+                             int32_t w, float* S_cube, int32_t* best_idx, float* best_ABC,
+                             float* best_S, float* stack_out, void* stream) {
+    SearchParams p;
+    TuneKey key;
+    int rc = build_crs_params(d, ap, A, nA, B, nB, C, nC, w, S_cube, best_idx, best_ABC, best_S,
+                              stack_out, &p, &key);
+    if (rc) return rc;
     cudaError_t e = launch_search(p, true, w, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "crs_semblance launch");
     return SEIS_OK;

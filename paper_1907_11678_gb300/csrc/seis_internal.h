@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "seis.h"
 
 namespace seis {
 
@@ -39,11 +40,85 @@ struct SearchParams {
     int variant;               // search kernel variant (tile shape / arithmetic form)
 };
 
+struct EvalParams {
+    const float* traces;
+    const int64_t* trace_off;
+    const float* h;
+    const float* m;
+    const int64_t* list_off;
+    const int32_t* list;
+    const float* m_c;
+    const int64_t* out_off;
+    const float* dt;
+    int64_t nowner;
+    int tiles_per_owner;      // ceil(max_rows / 128)
+    const float* theta;       // [rows][nparam]
+    int nparam;               // 1 (C, CMP) or 3 (A, B, C)
+    float* S;                 // [rows] or nullptr
+    float* stack;             // [rows] or nullptr
+    int32_t* N;               // [rows] or nullptr
+    float* grad;              // [rows][3] or nullptr (CRS only)
+    unsigned* status;
+};
+
+// One refinement step per row (reading c16: projected normalised-gradient ascent).  State:
+// theta/S/grad/stack = accepted point, trial_* = the last evaluated trial, step (< 0 once
+// the gradient vanished: no further trials).  If `judge`, the trial is accepted when its S is
+// not lower, else the step halves.  If `propose`, the next trial is formed.
+struct RefineParams {
+    int64_t rows;
+    float* theta;
+    float* S;
+    float* grad;
+    float* stack;
+    float* trial_theta;
+    const float* trial_S;
+    const float* trial_grad;
+    const float* trial_stack;
+    float* step;
+    float lo[3], hi[3];
+    float step0;
+    int judge, propose, init;
+};
+
 // Launchers (return the cudaError_t of the launch).
 cudaError_t launch_search(const SearchParams& p, bool crs, int w, cudaStream_t stream);
+cudaError_t launch_eval(const EvalParams& p, bool crs, bool grad, int w, cudaStream_t s);
+cudaError_t launch_refine_update(const RefineParams& r, cudaStream_t s);
+int eval_tile_rows();
 int search_variant_count();
 const char* search_variant_name(int v);
 
 unsigned* device_status_word();   // this device's status word (module global)
 
+// Error reporting shared by the host entry points (thread-local message).
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* where);
+
+// Autotuner shape buckets: problems in one bucket share the fastest kernel variant.
+struct TuneKey {
+    int crs, w, cand_bucket, rows_bucket, fold_bucket;
+    bool operator<(const TuneKey& o) const {
+        if (crs != o.crs) return crs < o.crs;
+        if (w != o.w) return w < o.w;
+        if (cand_bucket != o.cand_bucket) return cand_bucket < o.cand_bucket;
+        if (rows_bucket != o.rows_bucket) return rows_bucket < o.rows_bucket;
+        return fold_bucket < o.fold_bucket;
+    }
+};
+TuneKey make_tune_key(bool crs, int w, int ncand, int64_t max_rows, int64_t mean_fold);
+int lookup_variant(const TuneKey& k, int fallback);
+int default_variant();
+
+}  // namespace seis
+
+namespace seis {
+struct TuneKey;
+int build_cmp_params(const seis_gathers* d, const float* C, int32_t nc, int32_t w, float* S_cube,
+                     int32_t* best_idx, float* best_C, float* best_S, float* stack_out,
+                     SearchParams* out, TuneKey* key);
+int build_crs_params(const seis_gathers* d, const seis_aperture* ap, const float* A, int32_t nA,
+                     const float* B, int32_t nB, const float* C, int32_t nC, int32_t w,
+                     float* S_cube, int32_t* best_idx, float* best_ABC, float* best_S,
+                     float* stack_out, SearchParams* out, TuneKey* key);
 }  // namespace seis

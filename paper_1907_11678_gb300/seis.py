@@ -71,9 +71,23 @@ def load_library(path: str | None = None):
             lib.seis_search_variant_name.restype = ctypes.c_char_p
             lib.seis_search_variant_name.argtypes = [ctypes.c_int]
             lib.seis_set_search_variant.argtypes = [ctypes.c_int]
+            lib.seis_autotune_cmp.argtypes = [vp, vp, i32, i32, vp, vp, vp, i32, vp, vp, vp]
+            lib.seis_autotune_crs.argtypes = [vp, vp, vp, i32, vp, i32, vp, i32, i32, vp, vp, vp,
+                                              i32, vp, vp, vp]
+            lib.stack.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+            lib.crs_semblance_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
+            lib.seis_refine_workspace_size.argtypes = [i64]
+            lib.seis_refine_workspace_size.restype = ctypes.c_size_t
+            lib.crs_refine.argtypes = [vp, vp, vp, vp, vp, i32, f32, i32, vp, vp, vp, vp,
+                                       ctypes.c_size_t, i64, vp]
+            lib.seis_autotune_save.argtypes = [ctypes.c_char_p]
+            lib.seis_autotune_load.argtypes = [ctypes.c_char_p]
             for name in ("seis_device_status", "cmp_semblance", "crs_semblance",
                          "seis_crs_aperture", "seis_search_variant_count",
-                         "seis_set_search_variant", "seis_get_search_variant"):
+                         "seis_set_search_variant", "seis_get_search_variant",
+                         "seis_autotune_cmp", "seis_autotune_crs", "seis_autotune_save",
+                         "seis_autotune_load", "seis_autotune_clear", "stack",
+                         "crs_semblance_grad", "crs_refine"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -251,6 +265,132 @@ def set_search_variant(v: int) -> None:
 
 def get_search_variant() -> int:
     return int(load_library().seis_get_search_variant())
+
+
+def autotune_cmp(g: Gathers, C: torch.Tensor, w: int = 11, reps: int = 2, stream=None):
+    """Time every search-kernel variant on this CMP problem (include/seis.h:
+    seis_autotune_cmp); later calls in the same shape bucket use the fastest.  Returns
+    (chosen variant, list of mean milliseconds per variant)."""
+    lib = load_library()
+    dev = g.traces.device
+    bi = torch.empty(g.rows, dtype=torch.int32, device=dev)
+    bs = torch.empty(g.rows, dtype=torch.float32, device=dev)
+    st = torch.empty(g.rows, dtype=torch.float32, device=dev)
+    nv = lib.seis_search_variant_count()
+    ms = (ctypes.c_float * nv)()
+    chosen = ctypes.c_int32(-1)
+    _check(lib.seis_autotune_cmp(ctypes.byref(g.descriptor()), _ptr(C), int(C.numel()), w,
+                                 _ptr(bi), _ptr(bs), _ptr(st), reps, ctypes.byref(chosen), ms,
+                                 _stream_handle(stream)))
+    return int(chosen.value), list(ms)
+
+
+def autotune_crs(g: Gathers, ap: "Aperture", A, B, C, w: int = 11, reps: int = 2, stream=None):
+    """As autotune_cmp for a CRS problem (include/seis.h: seis_autotune_crs)."""
+    lib = load_library()
+    dev = g.traces.device
+    bi = torch.empty(ap.rows, dtype=torch.int32, device=dev)
+    bs = torch.empty(ap.rows, dtype=torch.float32, device=dev)
+    st = torch.empty(ap.rows, dtype=torch.float32, device=dev)
+    nv = lib.seis_search_variant_count()
+    ms = (ctypes.c_float * nv)()
+    chosen = ctypes.c_int32(-1)
+    _check(lib.seis_autotune_crs(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
+                                 _ptr(A), int(A.numel()), _ptr(B), int(B.numel()), _ptr(C),
+                                 int(C.numel()), w, _ptr(bi), _ptr(bs), _ptr(st), reps,
+                                 ctypes.byref(chosen), ms, _stream_handle(stream)))
+    return int(chosen.value), list(ms)
+
+
+def autotune_save(path: str) -> None:
+    _check(load_library().seis_autotune_save(path.encode()))
+
+
+def autotune_load(path: str) -> None:
+    _check(load_library().seis_autotune_load(path.encode()))
+
+
+def autotune_clear() -> None:
+    _check(load_library().seis_autotune_clear())
+
+
+def stack(g: Gathers, ap: "Aperture | None", params: torch.Tensor, w: int = 11,
+          stream=None) -> dict:
+    """Stack (and semblance, trace count) along one operator per output row
+    (include/seis.h: stack).  ap None: CMP, params [rows] = C; else CRS, params [rows, 3]."""
+    lib = load_library()
+    dev = g.traces.device
+    rows = g.rows if ap is None else ap.rows
+    params = params.contiguous()
+    out = dict(stack=torch.empty(rows, dtype=torch.float32, device=dev),
+               S=torch.empty(rows, dtype=torch.float32, device=dev),
+               N=torch.empty(rows, dtype=torch.int32, device=dev))
+    _check(lib.stack(ctypes.byref(g.descriptor()),
+                     None if ap is None else ctypes.byref(ap.descriptor()), _ptr(params), w,
+                     _ptr(out["stack"]), _ptr(out["S"]), _ptr(out["N"]), _stream_handle(stream)))
+    return out
+
+
+def crs_semblance_grad(g: Gathers, ap: "Aperture", ABC: torch.Tensor, w: int = 11,
+                       stream=None):
+    """Semblance, dS/d(A,B,C) [rows, 3] and stack at ABC [rows, 3] (adjoint kernel)."""
+    lib = load_library()
+    dev = g.traces.device
+    ABC = ABC.contiguous()
+    S = torch.empty(ap.rows, dtype=torch.float32, device=dev)
+    grad = torch.empty((ap.rows, 3), dtype=torch.float32, device=dev)
+    st = torch.empty(ap.rows, dtype=torch.float32, device=dev)
+    _check(lib.crs_semblance_grad(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
+                                  _ptr(ABC), w, _ptr(S), _ptr(grad), _ptr(st),
+                                  _stream_handle(stream)))
+    return S, grad, st
+
+
+def crs_refine(g: Gathers, ap: "Aperture", ABC0: torch.Tensor, lo3, hi3, steps: int = 20,
+               step0: float = 0.05, w: int = 11, stream=None, workspace=None) -> dict:
+    """Gradient-ascent refinement of CRS operators from ABC0 [rows, 3] (include/seis.h:
+    crs_refine).  Returns theta, S, grad, stack (device tensors)."""
+    lib = load_library()
+    dev = g.traces.device
+    theta = ABC0.detach().clone().contiguous().float()
+    S = torch.empty(ap.rows, dtype=torch.float32, device=dev)
+    grad = torch.empty((ap.rows, 3), dtype=torch.float32, device=dev)
+    st = torch.empty(ap.rows, dtype=torch.float32, device=dev)
+    nbytes = lib.seis_refine_workspace_size(ap.rows)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    lo = (ctypes.c_float * 3)(*[float(v) for v in lo3])
+    hi = (ctypes.c_float * 3)(*[float(v) for v in hi3])
+    _check(lib.crs_refine(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
+                          _ptr(theta), lo, hi, int(steps), ctypes.c_float(step0), w, _ptr(S),
+                          _ptr(grad), _ptr(st), ctypes.c_void_p(aligned),
+                          workspace.numel() - (aligned - base), ap.rows, _stream_handle(stream)))
+    return dict(theta=theta, S=S, grad=grad, stack=st)
+
+
+class CRSSemblance(torch.autograd.Function):
+    """S(A, B, C) per output row as a differentiable function of the operators [rows, 3]:
+    forward runs the evaluation kernel, backward the hand-written adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, ABC, g, ap, w=11):
+        out = stack(g, ap, ABC.detach().float(), w)
+        ctx.save_for_backward(ABC.detach())
+        ctx.g, ctx.ap, ctx.w = g, ap, w
+        return out["S"]
+
+    @staticmethod
+    def backward(ctx, grad_S):
+        (ABC,) = ctx.saved_tensors
+        _, dS, _ = crs_semblance_grad(ctx.g, ctx.ap, ABC.float(), ctx.w)
+        return grad_S.unsqueeze(1) * dS, None, None, None
+
+
+def crs_semblance_at(ABC: torch.Tensor, g: Gathers, ap: "Aperture", w: int = 11):
+    """Differentiable semblance of one CRS operator per row (see CRSSemblance)."""
+    return CRSSemblance.apply(ABC, g, ap, w)
 
 
 def device_status(stream=None) -> None:

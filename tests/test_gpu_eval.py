@@ -1,0 +1,152 @@
+"""Per-row operator evaluation on the GPU (stack, adjoint, refinement, autograd) against
+the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_11678_gb300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def seis():
+    from paper_1907_11678_gb300 import build, seis as s
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return s
+
+
+def _nb_of(ap):
+    return (ap.nbr_off.cpu().numpy(), ap.nbr_trace.cpu().numpy()[:int(ap.nbr_off[-1])],
+            ap.m_c.cpu().numpy(), ap.out_off.cpu().numpy(), ap.dt.cpu().numpy())
+
+
+def _ranges():
+    (alo, ahi), (blo, bhi), (clo, chi) = synth.crs_ranges()
+    return np.array([alo, blo, clo]), np.array([ahi, bhi, chi])
+
+
+@pytest.fixture(scope="module")
+def line(seis):
+    ds = synth.crs_line(20, 12, 500, 0.004, 0.0, 1800.0, 3, 2, 2.0, seed=61)
+    g = seis.to_device(ds)
+    ap = seis.crs_aperture(g, np.arange(4, 16), 50.0)
+    return ds, g, ap
+
+
+def _random_theta(rows, seed, shrink=0.6):
+    lo, hi = _ranges()
+    rng = np.random.default_rng(seed)
+    mid, half = (lo + hi) / 2, (hi - lo) / 2 * shrink
+    th = mid + half * rng.uniform(-1, 1, (rows, 3))
+    th[:, 2] = rng.uniform(lo[2], hi[2], rows)
+    return th.astype(np.float32)
+
+
+def test_stack_cmp_matches_oracle(seis):
+    ds = synth.cmp_line(5, 14, 400, 0.004, 0.0, 1600.0, 3, 2.0, seed=71)
+    g = seis.to_device(ds)
+    rows = int(ds["out_off"][-1])
+    rng = np.random.default_rng(3)
+    C = np.float32(4.0 / rng.uniform(1400, 4500, rows) ** 2)
+    out = seis.stack(g, None, torch.from_numpy(C).cuda(), w=11)
+    torch.cuda.synchronize()
+    seis.device_status()
+    th = np.stack([np.zeros(rows), np.zeros(rows), C.astype(np.float64)], 1)
+    ref = oracle.crs_eval(ds, oracle.cmp_as_crs(ds), th)
+    np.testing.assert_array_equal(out["N"].cpu().numpy(), ref.N)
+    dS = np.abs(out["S"].cpu().numpy() - ref.S).max()
+    st = out["stack"].cpu().numpy()
+    rel = np.linalg.norm(st - ref.stack) / np.linalg.norm(ref.stack)
+    print(f"[parity] stack-cmp: max dS {dS:.2e} stack rel L2 {rel:.2e}")
+    assert dS <= parity.S_TOL and rel <= parity.STACK_TOL
+
+
+def test_stack_matches_search_pick(seis):
+    """stack() at the search's picked C reproduces the search's stack and best S bit for bit."""
+    ds = synth.cmp_line(3, 16, 300, 0.004, 0.0, 1500.0, 3, 2.0, seed=72)
+    g = seis.to_device(ds)
+    C = torch.from_numpy(oracle.velocity_grid(1400, 4500, 61).astype(np.float32)).cuda()
+    srch = seis.cmp_semblance(g, C, w=11)
+    out = seis.stack(g, None, srch["best_C"], w=11)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out["stack"].cpu().numpy(), srch["stack"].cpu().numpy())
+    np.testing.assert_array_equal(out["S"].cpu().numpy(), srch["best_S"].cpu().numpy())
+
+
+def test_stack_crs_matches_oracle(seis, line):
+    ds, g, ap = line
+    th = _random_theta(ap.rows, 5)
+    out = seis.stack(g, ap, torch.from_numpy(th).cuda(), w=11)
+    torch.cuda.synchronize()
+    seis.device_status()
+    ref = oracle.crs_eval(ds, _nb_of(ap), th.astype(np.float64))
+    N = out["N"].cpu().numpy()
+    agree = N == ref.N
+    assert agree.mean() > 0.995
+    dS = np.abs(out["S"].cpu().numpy() - ref.S)[agree].max()
+    st = out["stack"].cpu().numpy()
+    rel = np.linalg.norm((st - ref.stack)[agree]) / np.linalg.norm(ref.stack[agree])
+    print(f"[parity] stack-crs: max dS {dS:.2e} stack rel L2 {rel:.2e} N agree {agree.mean():.4f}")
+    assert dS <= parity.S_TOL and rel <= parity.STACK_TOL
+
+
+def test_adjoint_matches_oracle_gradient(seis, line):
+    ds, g, ap = line
+    th = _random_theta(ap.rows, 6)
+    S, grad, st = seis.crs_semblance_grad(g, ap, torch.from_numpy(th).cuda(), w=11)
+    torch.cuda.synchronize()
+    seis.device_status()
+    ref = oracle.crs_eval(ds, _nb_of(ap), th.astype(np.float64))
+    G = grad.cpu().numpy().astype(np.float64)
+    live = ref.S > 0.05
+    for a, name in enumerate("ABC"):
+        e = G[live, a] - ref.grad[live, a]
+        rel = np.linalg.norm(e) / np.linalg.norm(ref.grad[live, a])
+        med = np.median(np.abs(e) / (np.abs(ref.grad[live, a]) + 1e-12))
+        print(f"[parity] grad d/d{name}: rel L2 {rel:.2e}, median row rel {med:.2e}")
+        assert rel <= 1e-3 and med <= 1e-3
+    assert np.abs(S.cpu().numpy() - ref.S).max() <= parity.S_TOL
+
+
+def test_autograd_function_uses_adjoint(seis, line):
+    ds, g, ap = line
+    th = torch.from_numpy(_random_theta(ap.rows, 7)).cuda().requires_grad_(True)
+    S = seis.crs_semblance_at(th, g, ap, 11)
+    wts = torch.linspace(0.5, 1.5, ap.rows, device="cuda")
+    (S * wts).sum().backward()
+    S2, dS, _ = seis.crs_semblance_grad(g, ap, th.detach(), w=11)
+    torch.testing.assert_close(S.detach(), S2, rtol=0, atol=0)
+    torch.testing.assert_close(th.grad, wts[:, None] * dS, rtol=0, atol=0)
+
+
+def test_refine_monotone_and_consistent(seis, line):
+    ds, g, ap = line
+    lo, hi = _ranges()
+    A = np.float32(np.linspace(lo[0], hi[0], 7)); B = np.float32(np.linspace(lo[1], hi[1], 7))
+    C = np.float32(np.linspace(lo[2], hi[2], 11))
+    t = lambda a: torch.from_numpy(a).cuda()
+    coarse = seis.crs_semblance(g, ap, t(A), t(B), t(C), w=11)
+    th0 = coarse["best_ABC"]
+    r = seis.crs_refine(g, ap, th0, lo, hi, steps=20, step0=0.05, w=11)
+    torch.cuda.synchronize()
+    seis.device_status()
+    S0 = coarse["best_S"].cpu().numpy()
+    S1 = r["S"].cpu().numpy()
+    th1 = r["theta"].cpu().numpy()
+    assert np.all(S1 >= S0 - 1e-6)
+    assert np.all(th1 >= np.float32(lo) - 1e-12) and np.all(th1 <= np.float32(hi) + 1e-12)
+    # the reported S and stack are those of the reported operator
+    ref_at = oracle.crs_eval(ds, _nb_of(ap), th1.astype(np.float64))
+    assert np.abs(S1 - ref_at.S).max() <= parity.S_TOL
+    # against the oracle's own refinement from the same start
+    ref = oracle.crs_refine(ds, _nb_of(ap), th0.cpu().numpy().astype(np.float64), lo, hi,
+                            steps=20, step0=0.05)
+    close = np.abs(S1 - ref.S) <= 1e-3
+    print(f"[parity] refine: gain {np.mean(S1 - S0):.4f}, |S_gpu - S_oracle| <= 1e-3 on "
+          f"{close.mean():.3f} of rows, mean diff {np.mean(S1 - ref.S):+.2e}")
+    assert close.mean() >= 0.9

@@ -88,3 +88,32 @@ def test_misaligned_traces_is_einval(lib):
     rc = lib.cmp_semblance(ctypes.byref(g), fake, ctypes.c_int32(3), ctypes.c_int32(11),
                            None, fake, None, fake, fake, None)
     assert rc == -1 and "aligned" in _err(lib)
+
+
+def test_autotune_cache_roundtrip(lib, tmp_path):
+    """The autotune table saves and loads as JSON without a GPU (host logic only)."""
+    lib.seis_autotune_save.argtypes = [ctypes.c_char_p]
+    lib.seis_autotune_load.argtypes = [ctypes.c_char_p]
+    p = tmp_path / "tune.json"
+    p.write_text('{"format": "seis-autotune-1", "entries": [\n'
+                 '  {"crs": 0, "w": 11, "cand_bucket": 7, "rows_bucket": 10, "fold_bucket": 5, "variant": 3},\n'
+                 '  {"crs": 1, "w": 11, "cand_bucket": 14, "rows_bucket": 10, "fold_bucket": 0, "variant": 1}\n]}\n')
+    assert lib.seis_autotune_clear() == 0
+    assert lib.seis_autotune_load(str(p).encode()) == 0
+    out = tmp_path / "out.json"
+    assert lib.seis_autotune_save(str(out).encode()) == 0
+    txt = out.read_text()
+    assert '"variant": 3' in txt and '"variant": 1' in txt and txt.count('"crs"') == 2
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"entries": [{"crs": 0, "w": 11, "cand_bucket": 7, "rows_bucket": 10, '
+                   '"fold_bucket": 5, "variant": 99}]}')
+    assert lib.seis_autotune_load(str(bad).encode()) == -1
+    assert lib.seis_autotune_clear() == 0
+
+
+def test_variant_selector(lib):
+    n = lib.seis_search_variant_count()
+    assert n >= 2
+    assert lib.seis_set_search_variant(n) == -1
+    assert lib.seis_set_search_variant(0) == 0 and lib.seis_get_search_variant() == 0
+    assert lib.seis_set_search_variant(5) == 0
