@@ -189,8 +189,10 @@ def crs_semblance(ds, nb, A, B, C, w=11, rows=None, want_cube=False, knot_eps=1e
     return Result(S=S, N=N, edge=edge, best_idx=bi, best_S=bs, second_S=b2, stack=st)
 
 
-def crs_eval(ds, nb, theta, w=11, rows=None, nthreads=0) -> Result:
-    """S, dS/d(A,B,C) and stack at one operator per row (theta [nrows, 3])."""
+def crs_eval(ds, nb, theta, w=11, rows=None, knot_eps=1e-4, nthreads=0) -> Result:
+    """S, dS/d(A,B,C) and stack at one operator per row (theta [nrows, 3]).  ``knot`` flags
+    rows where a trace lies within knot_eps*(1 + 3e-3 u) samples of a sample point or a
+    mask edge (the gradient is defined almost everywhere; FP32 may land on either side)."""
     lib = _load()
     arrs = _crs_common(ds, nb)
     ncen = len(arrs[6])
@@ -201,12 +203,14 @@ def crs_eval(ds, nb, theta, w=11, rows=None, nthreads=0) -> Result:
     grad = np.empty((nrows, 3), np.float64)
     st = np.empty(nrows, np.float64)
     N = np.empty(nrows, np.int32)
+    knot = np.empty(nrows, np.int8)
     rc = lib.seis_oracle_crs_eval(*[_p(a) for a in arrs], ctypes.c_int64(ncen), ctypes.c_int32(w),
                                   _p(rows_a), ctypes.c_int64(nrows), _p(theta),
-                                  _p(S), _p(grad), _p(st), _p(N), ctypes.c_int32(nthreads))
+                                  _p(S), _p(grad), _p(st), _p(N), _p(knot),
+                                  ctypes.c_double(knot_eps), ctypes.c_int32(nthreads))
     if rc != 0:
         raise ValueError("seis_oracle_crs_eval: invalid arguments")
-    return Result(S=S, grad=grad, stack=st, N=N)
+    return Result(S=S, grad=grad, stack=st, N=N, knot=knot != 0)
 
 
 def crs_refine(ds, nb, theta0, lo3, hi3, steps=20, step0=0.05, w=11, rows=None,

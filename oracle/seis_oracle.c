@@ -346,8 +346,10 @@ int seis_oracle_crs(const float* traces, const int64_t* trace_off, const float* 
 static void crs_eval_one(const float* traces, const int64_t* trace_off, const float* h,
                          const float* m, const int32_t* list, int64_t cnt, double mc,
                          double t0, double dtg, int hw, const double* th,
-                         double* S_out, double* grad_out, double* stack_out, int32_t* N_out)
+                         double* S_out, double* grad_out, double* stack_out, int32_t* N_out,
+                         int8_t* knot_out, double knot_eps)
 {
+    int knot = 0;
     const int w = 2 * hw + 1;
     double num[ORACLE_MAXW], dnum[3][ORACLE_MAXW];
     double den = 0.0, ac = 0.0, dden[3] = {0.0, 0.0, 0.0};
@@ -361,6 +363,12 @@ static void crs_eval_one(const float* traces, const int64_t* trace_off, const fl
         const int64_t ns_i = trace_off[i + 1] - trace_off[i];
         double u, p, t;
         if (!crs_time(t0, th[0], th[1], th[2], dm, hh, dtg, &u, &p, &t)) continue;
+        /* knot bookkeeping for FP32 parity of the gradient (defined almost everywhere):
+         * u within the FP32 error of u of a sample, or a mask edge within it */
+        if (knot_out && !zero_moveout(th[0], th[1], th[2], dm, hh)) {
+            const double tol = knot_eps * (1.0 + 3.0e-3 * u);
+            if (fabs(u - floor(u + 0.5)) < tol || edge_sensitive(u, ns_i, hw, tol)) knot = 1;
+        }
         if (!window_inside(u, ns_i, hw)) continue;
         const float* f = traces + trace_off[i];
         const double kf = floor(u);
@@ -403,6 +411,7 @@ static void crs_eval_one(const float* traces, const int64_t* trace_off, const fl
     }
     if (stack_out) *stack_out = N ? ac / ((double)N * w) : 0.0;
     if (N_out) *N_out = (int32_t)N;
+    if (knot_out) *knot_out = (int8_t)knot;
 }
 
 /* Evaluate S, dS/d(A,B,C) and the stack at given operators, one per row. */
@@ -412,7 +421,7 @@ int seis_oracle_crs_eval(const float* traces, const int64_t* trace_off, const fl
                          int64_t n_central, int32_t w,
                          const int64_t* rows, int64_t nrows, const double* theta,
                          double* S, double* grad, double* stack, int32_t* Nvalid,
-                         int32_t nthreads)
+                         int8_t* knot, double knot_eps, int32_t nthreads)
 {
     if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || n_central < 1) return -1;
     const int hw = w / 2;
@@ -427,7 +436,7 @@ int seis_oracle_crs_eval(const float* traces, const int64_t* trace_off, const fl
         double s, st; int32_t N;
         crs_eval_one(traces, trace_off, h, m, nbr_trace + nbr_off[c], nbr_off[c + 1] - nbr_off[c],
                      (double)m_c[c], (double)n * dtg, dtg, hw, theta + 3 * e,
-                     &s, grad ? grad + 3 * e : NULL, &st, &N);
+                     &s, grad ? grad + 3 * e : NULL, &st, &N, knot ? knot + e : NULL, knot_eps);
         if (S) S[e] = s;
         if (stack) stack[e] = st;
         if (Nvalid) Nvalid[e] = N;
@@ -471,7 +480,8 @@ int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const 
             z[a] = (theta_in[3 * e + a] - lo3[a]) / (hi3[a] - lo3[a]);
             th[a] = theta_in[3 * e + a];
         }
-        crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th, &s, g, &st, NULL);
+        crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th, &s, g, &st, NULL,
+                     NULL, 0.0);
         double step = step0;
         for (int it = 0; it < steps; ++it) {
             double gn = 0.0;
@@ -484,7 +494,8 @@ int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const 
                 z2[a] = zz < 0.0 ? 0.0 : (zz > 1.0 ? 1.0 : zz);
                 th2[a] = lo3[a] + z2[a] * (hi3[a] - lo3[a]);
             }
-            crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th2, &s2, g2, &st2, NULL);
+            crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th2, &s2, g2, &st2,
+                         NULL, NULL, 0.0);
             if (s2 >= s) {
                 for (int a = 0; a < 3; ++a) { z[a] = z2[a]; th[a] = th2[a]; g[a] = g2[a]; }
                 s = s2; st = st2;

