@@ -83,8 +83,10 @@ typedef struct seis_aperture {
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* seis_last_error(void);
 
-/* SYNCHRONOUS.  Waits for `stream`, then returns SEIS_OK, or SEIS_ETIMEOUT if a kernel of
- * this library recorded a timed-out device wait since the last call (and clears it). */
+/* SYNCHRONOUS.  Waits for `stream`, then reports (and clears) what kernels of this library
+ * recorded in the device status word since the last call: SEIS_ETIMEOUT (a bounded device
+ * wait gave up), SEIS_EUNSUPPORTED (a staged window overflowed), SEIS_EINVAL (a batch item
+ * was skipped), else SEIS_OK. */
 int seis_device_status(void* stream);
 
 /* Search kernel variants.  The semblance search kernels come in several tile shapes and
@@ -197,6 +199,42 @@ int crs_refine(const seis_gathers* d, const seis_aperture* ap, float* ABC_inout,
                const float* lo3, const float* hi3, int32_t steps, float step0, int32_t w,
                float* S_out, float* grad_out, float* stack_out,
                void* workspace, size_t ws_bytes, int64_t rows, void* stream);
+
+/* Batched search (no counterpart in the paper: its CGs take one CDP per task, Section 3.5;
+ * here thousands of uneven CMP gathers and CRS supergathers run in ONE persistent launch
+ * that can be captured in a CUDA graph).  Item i owns the traces
+ * [trace_begin, trace_end) of d (a CRS item's traces carry their own midpoints, so the
+ * item is its own aperture), the output rows [out_begin, out_begin + rows) at t0 = n*dt,
+ * and the candidate axes A = poolA[a_off .. a_off+nA), B = poolB[b_off ..), C = poolC[c_off
+ * ..) searched as cand = (ia*nB + ib)*nC + ic (CMP items: nA = nB = 1, A and B ignored).
+ * Results as crs_semblance (best_ABC holds (0, 0, C) for CMP items).  Items with an
+ * out-of-range field are skipped and flagged in the device status word. */
+typedef struct seis_batch_item {
+    int64_t trace_begin, trace_end;
+    int64_t out_begin;
+    int32_t rows;
+    int32_t kind;            /* 0 = CMP gather, 1 = CRS supergather */
+    float   dt;              /* s */
+    float   m_c;             /* CRS: central midpoint (m) */
+    int32_t a_off, nA;
+    int32_t b_off, nB;
+    int32_t c_off, nC;
+} seis_batch_item;
+
+/* Device scratch of seis_batch_workspace_size(nitems) bytes (256-byte aligned, caller-owned)
+ * holds the work counter and the task table; every call rebuilds it.
+ *   items: device [nitems]; pool sizes are host values used for the range checks;
+ *   out_rows (host) = length of the output arrays (best_ABC: 3 * out_rows floats).
+ *   mode 0: one persistent launch (grid = 2 CTAs per SM, tasks claimed from the counter);
+ *   mode 1: one launch per item (the comparison; SYNCHRONOUS: reads the item table back).
+ * d: traces, trace_off, half_offset, midpoint (needed when an item is CRS); gather fields
+ * are not used.  Errors: SEIS_EINVAL, SEIS_ECUDA. */
+size_t seis_batch_workspace_size(int64_t nitems);
+int seis_batch_semblance(const seis_gathers* d, const seis_batch_item* items, int64_t nitems,
+                         const float* poolA, int32_t sizeA, const float* poolB, int32_t sizeB,
+                         const float* poolC, int32_t sizeC, int32_t w, int32_t mode,
+                         int32_t* best_idx, float* best_ABC, float* best_S, float* stack_out,
+                         int64_t out_rows, void* workspace, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,266 @@
+// batch_kernel.cuh -- one persistent launch over thousands of uneven CMP gathers and CRS
+// supergathers (seis_batch_semblance).
+//
+// Same arithmetic as the search kernel (Eq. 1, Algorithm 1, Section 3.2 argmax and stack;
+// CMP items run through the CRS traveltime with dm = 0 and A = B = 0, which reproduces the
+// CMP traveltime bit for bit).  Work unit = task = (item, tile of 32 output rows).  The
+// producer warp of each resident CTA claims tasks from a device counter (the task table is
+// ordered as the items, so callers put costly items first) and streams their stages through
+// the shared-memory ring without a break at task boundaries; the consumer warps finish a
+// task's argmax when its last pass ends and go on with the next task's stages.
+#pragma once
+#include "search_kernel.cuh"
+
+namespace seis {
+
+struct ItemView {
+    int64_t lbeg;
+    int M;
+    int64_t row0;
+    int nrows;
+    float dt, mc;
+    int kind, a_off, nA, b_off, nB, c_off, nC, ncand;
+};
+
+__device__ __forceinline__ ItemView load_item(const BatchParams& P, int64_t i) {
+    const seis_batch_item it = P.items[i];
+    ItemView v;
+    v.lbeg = it.trace_begin;
+    v.M = (int)(it.trace_end - it.trace_begin);
+    v.row0 = it.out_begin;
+    v.nrows = it.rows;
+    v.dt = it.dt;
+    v.mc = it.m_c;
+    v.kind = it.kind;
+    v.a_off = it.a_off;
+    v.nA = it.kind ? it.nA : 1;
+    v.b_off = it.b_off;
+    v.nB = it.kind ? it.nB : 1;
+    v.c_off = it.c_off;
+    v.nC = it.nC;
+    v.ncand = v.nA * v.nB * v.nC;
+    return v;
+}
+
+__device__ __forceinline__ void decode_item(const BatchParams& P, const ItemView& v, int c,
+                                            float& a, float& b, float& cc) {
+    const int nbc = v.nB * v.nC;
+    const int ia = c / nbc;
+    const int rem = c - ia * nbc;
+    const int ib = rem / v.nC;
+    const int ic = rem - ib * v.nC;
+    a = v.kind ? P.poolA[v.a_off + ia] : 0.f;
+    b = v.kind ? P.poolB[v.b_off + ib] : 0.f;
+    cc = P.poolC[v.c_off + ic];
+}
+
+// Largest item i in [lo, hi) with task_off[i] <= t.
+__device__ __forceinline__ int64_t item_of_task(const int64_t* task_off, int64_t lo, int64_t hi,
+                                                int64_t t) {
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) / 2;
+        if (task_off[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int W, class CFG>
+__global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchParams P) {
+    constexpr int HW = W / 2;
+    constexpr int kWarps = CFG::kWarps;
+    constexpr int kR = CFG::kR;
+    constexpr int kCB = CFG::kCB;
+    constexpr int kConsumers = CFG::kConsumers;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SearchSmem& sm = *reinterpret_cast<SearchSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t t_begin = P.task_off[P.item_begin];
+    const int64_t t_end = P.task_off[P.item_end];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(&sm.full[s], 32);
+            mbar_init(&sm.empty[s], kConsumers);
+        }
+        sm.abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (threadIdx.x < 16) sm.zeros[threadIdx.x] = 0.f;
+    __syncthreads();
+
+    if (warp == kWarps) {
+        // =============================== producer warp ================================
+        bool have = false;
+        ItemView it{};
+        int64_t item = 0;
+        int tile = 0, n0 = 0, n_last = 0, npass = 0;
+        int pl_pass = 0, pl_t = 0, pl_bpass = -1;
+        float bA0 = 0.f, bA1 = 0.f, bB0 = 0.f, bB1 = 0.f, bC0 = 0.f, bC1 = 0.f;
+        int s = 0;
+        for (;; ++s) {
+            const int slot = s % kSlots;
+            if (s >= kSlots && !sm.abort_flag) {
+                if (!mbar_wait_bounded(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
+                    sm.abort_flag = 1;
+                    record_status(P.status, kStatusTimeout);
+                }
+            }
+            __syncwarp();
+            bool finished = sm.abort_flag != 0;
+            if (!finished && (!have || pl_pass >= npass)) {
+                unsigned long long t = 0;
+                if (lane == 0) t = atomicAdd(P.counter, 1ull);
+                t = __shfl_sync(kFull, t, 0);
+                const int64_t tk = t_begin + (int64_t)t;
+                if (tk >= t_end) {
+                    finished = true;
+                } else {
+                    item = item_of_task(P.task_off, P.item_begin, P.item_end, tk);
+                    tile = (int)(tk - P.task_off[item]);
+                    it = load_item(P, item);
+                    n0 = tile * 32;
+                    n_last = min(n0 + 31, it.nrows - 1);
+                    npass = (it.ncand + kCB - 1) / kCB;
+                    pl_pass = 0;
+                    pl_t = 0;
+                    pl_bpass = -1;
+                    have = true;
+                }
+            }
+            if (finished) {
+                if (lane == 0) sm.desc[slot] = StageDesc{0, 0, 0, 0, 1, 0, 0, 0};
+                __syncwarp();
+                mbar_arrive(&sm.full[slot]);
+                break;
+            }
+            if (pl_bpass != pl_pass) {   // candidate bounds of this pass (one per lane)
+                const int c = pl_pass * kCB + lane;
+                float a = 0.f, b = 0.f, cc = 0.f;
+                const bool v = lane < kCB && c < it.ncand;
+                if (v) decode_item(P, it, c, a, b, cc);
+                bA0 = warp_min(v ? a : FLT_MAX);  bA1 = warp_max(v ? a : -FLT_MAX);
+                bB0 = warp_min(v ? b : FLT_MAX);  bB1 = warp_max(v ? b : -FLT_MAX);
+                bC0 = warp_min(v ? cc : FLT_MAX); bC1 = warp_max(v ? cc : -FLT_MAX);
+                pl_bpass = pl_pass;
+            }
+            const int first = (pl_t == 0);
+            int nfit = 0;
+            const int ntr = produce_stage<true, HW>(
+                sm.buf[slot], sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h,
+                it.kind ? P.m : nullptr, nullptr, it.lbeg, it.M, pl_t, it.dt, it.mc, n0, n_last,
+                StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit);
+            pl_t += nfit;
+            const int last = (pl_t >= it.M);
+            const int task_end = last && (pl_pass + 1 >= npass);
+            if (lane == 0)
+                sm.desc[slot] = StageDesc{pl_pass, ntr, first, last, 0, (int)item, tile, task_end};
+            if (last) { ++pl_pass; pl_t = 0; }
+            __syncwarp();
+            mbar_arrive(&sm.full[slot]);
+        }
+        const int s_end = s;
+        for (int s2 = max(0, s_end - kSlots + 1); s2 <= s_end; ++s2)
+            mbar_wait_bounded(&sm.full[s2 % kSlots], (uint32_t)((s2 / kSlots) & 1));
+        return;
+    }
+
+    // ================================ consumer warps =====================================
+    const float* smf = reinterpret_cast<const float*>(smem_raw);
+    const int zidx = (int)(reinterpret_cast<const float*>(sm.zeros) - smf);
+    Accum<W, CFG> acc;
+    #pragma unroll
+    for (int r = 0; r < kR; ++r) acc.cidx[r] = INT_MAX;
+    ItemView it{};
+    RowConst rc = row_const(false, 0);
+    bool act = false;
+    int nrow = 0;
+    float bestS = -1.f, bestT = 0.f;
+    int bestC = INT_MAX;
+    auto decode = [&](int c, float& a, float& b, float& cc) { decode_item(P, it, c, a, b, cc); };
+
+    for (int s = 0;; ++s) {
+        const int slot = s % kSlots;
+        if (!mbar_wait_bounded(&sm.full[slot], (uint32_t)((s / kSlots) & 1))) {
+            sm.abort_flag = 1;
+            record_status(P.status, kStatusTimeout);
+            break;
+        }
+        const StageDesc d = sm.desc[slot];
+        if (d.end) break;
+        if (d.first && d.pass == 0) {            // a new task
+            it = load_item(P, d.pad0);
+            nrow = d.pad1 * 32 + lane;
+            act = nrow < it.nrows;
+            rc = row_const(act, nrow);
+        }
+        if (d.first) accum_begin(acc, d.pass * kCB + warp * kR, it.ncand, decode);
+        const int ntr = min(d.ntr, kChunkT);
+        const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
+        if (ntr > 0 && acc.cidx[0] < it.ncand)
+            accum_stage<true, W, CFG>(acc, sm.meta[slot], ntr, slot_base, rc, zidx, smf);
+        if (d.last) accum_end(acc, it.ncand, nullptr, bestS, bestC, bestT);
+        if (d.pad2) {                            // the task's last stage: argmax and outputs
+            sm.redS[warp][lane] = bestS;
+            sm.redC[warp][lane] = bestC;
+            sm.redT[warp][lane] = bestT;
+            consumer_bar(kConsumers);
+            if (warp == 0 && act) {
+                float bs, bt;
+                int bc;
+                reduce_best(sm, kWarps, lane, bs, bc, bt);
+                float a, b, cc;
+                decode_item(P, it, bc, a, b, cc);
+                const int64_t row = it.row0 + nrow;
+                P.best_idx[row] = bc;
+                P.best_S[row] = bs;
+                P.stack[row] = bt;
+                if (P.best_ABC) {
+                    P.best_ABC[row * 3 + 0] = a;
+                    P.best_ABC[row * 3 + 1] = b;
+                    P.best_ABC[row * 3 + 2] = cc;
+                }
+            }
+            consumer_bar(kConsumers);            // the reduction arrays are free again
+            bestS = -1.f;
+            bestT = 0.f;
+            bestC = INT_MAX;
+        }
+        mbar_arrive(&sm.empty[slot]);
+    }
+}
+
+template <int W, class CFG>
+cudaError_t launch_batch_w(const BatchParams& p, int grid, cudaStream_t stream) {
+    static bool configured[64] = {};
+    const int smem = (int)sizeof(SearchSmem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        e = cudaFuncSetAttribute(batch_kernel<W, CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) configured[dev] = true;
+    }
+    if (grid <= 0) return cudaSuccess;
+    batch_kernel<W, CFG><<<grid, CFG::kThreads, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+template <class CFG>
+cudaError_t launch_batch_cfg(const BatchParams& p, int w, int grid, cudaStream_t s) {
+    switch (w) {
+        case 1: return launch_batch_w<1, CFG>(p, grid, s);
+        case 3: return launch_batch_w<3, CFG>(p, grid, s);
+        case 5: return launch_batch_w<5, CFG>(p, grid, s);
+        case 7: return launch_batch_w<7, CFG>(p, grid, s);
+        case 9: return launch_batch_w<9, CFG>(p, grid, s);
+        case 11: return launch_batch_w<11, CFG>(p, grid, s);
+        case 13: return launch_batch_w<13, CFG>(p, grid, s);
+        case 15: return launch_batch_w<15, CFG>(p, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace seis

@@ -307,7 +307,7 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
         tm.q = (float)(hd * hd / (dtd * dtd));
         float aLo = 0.f, aHi = 0.f, rLo, rHi;
         if (CRS) {
-            const double dm = (double)mm[tid] - (double)mc;
+            const double dm = mm ? (double)mm[tid] - (double)mc : 0.0;   // no midpoints: CMP
             tm.e = (float)(dm / dtd);
             tm.g = (float)(dm * dm / (dtd * dtd));
             aLo = fminf(bA0 * tm.e, bA1 * tm.e);
@@ -370,6 +370,204 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
     }
     nfit_out = nfit;
     return ntr;
+}
+
+// ---- consumer-side accumulation, shared by the search kernel and the batch kernel -----
+
+// Per-thread accumulators of kR candidates for one output row.
+template <int W, class CFG>
+struct Accum {
+    static constexpr bool kP = CFG::kPairs;
+    static constexpr int kR = CFG::kR;
+    static constexpr int kG = kP ? kR / 2 : kR;      // accumulator groups per thread
+    f2_t num2[kP ? kG : 1][W];
+    f2_t den2[kP ? kG : 1][2];                       // even / odd window positions
+    float num1[kP ? 1 : kG][W];
+    float den1[kP ? 1 : kG][2];
+    int cntv[kR];
+    float Ar[kR], Br[kR], Cr[kR];
+    f2_t A2[kP ? kG : 1], B2[kP ? kG : 1], C2[kP ? kG : 1];
+    int cidx[kR];
+};
+
+// Row constants of one consumer thread.  Rows past the owner's end carry n = 2^24 so that
+// their k falls outside every trace; nf > 0 keeps sqrt(n^2 + Cq) + n > 0.
+struct RowConst {
+    int n;
+    float nf, nsq;
+    f2_t nf2, nsq2;
+};
+
+__device__ __forceinline__ RowConst row_const(bool act, int nrow) {
+    RowConst rc;
+    rc.n = act ? nrow : (1 << 24);
+    rc.nf = fmaxf((float)rc.n, 1e-30f);
+    rc.nsq = rc.nf * rc.nf;
+    rc.nf2 = pk2(rc.nf, rc.nf);
+    rc.nsq2 = pk2(rc.nsq, rc.nsq);
+    return rc;
+}
+
+// Start a pass: candidates c0 .. c0+kR-1 (those >= ncand are computed, then discarded).
+template <int W, class CFG, class Decode>
+__device__ __forceinline__ void accum_begin(Accum<W, CFG>& a, int c0, int ncand, Decode decode) {
+    #pragma unroll
+    for (int r = 0; r < CFG::kR; ++r) {
+        const int c = c0 + r;
+        a.cidx[r] = c;
+        a.Ar[r] = a.Br[r] = a.Cr[r] = 0.f;
+        if (c < ncand) decode(c, a.Ar[r], a.Br[r], a.Cr[r]);
+        a.cntv[r] = 0;
+    }
+    #pragma unroll
+    for (int g = 0; g < Accum<W, CFG>::kG; ++g) {
+        if constexpr (Accum<W, CFG>::kP) {
+            a.A2[g] = pk2(a.Ar[2 * g], a.Ar[2 * g + 1]);
+            a.B2[g] = pk2(a.Br[2 * g], a.Br[2 * g + 1]);
+            a.C2[g] = pk2(a.Cr[2 * g], a.Cr[2 * g + 1]);
+            a.den2[g][0] = a.den2[g][1] = 0ull;
+            #pragma unroll
+            for (int j = 0; j < W; ++j) a.num2[g][j] = 0ull;
+        } else {
+            a.den1[g][0] = a.den1[g][1] = 0.f;
+            #pragma unroll
+            for (int j = 0; j < W; ++j) a.num1[g][j] = 0.f;
+        }
+    }
+}
+
+// Accumulate the ntr staged traces of one slot.  Software pipeline: the traveltimes of
+// trace t+1 (long MUFU chains) are formed while the window of trace t is accumulated.
+template <bool CRS, int W, class CFG>
+__device__ __forceinline__ void accum_stage(Accum<W, CFG>& a, const TraceMeta* meta, int ntr,
+                                            int slot_base, const RowConst& rc, int zidx,
+                                            const float* smf) {
+    constexpr int HW = W / 2;
+    constexpr int kR = CFG::kR;
+    constexpr int kG = Accum<W, CFG>::kG;
+    int sI[kR];
+    float sX[kR];
+    bool sO[kR];
+    auto setup = [&](int t) {
+        const TraceConst tc = trace_const(meta[t], rc.n, slot_base, HW);
+        if constexpr (CFG::kMode == kPacked) {
+            #pragma unroll
+            for (int g = 0; g < kG; ++g)
+                intersect_pair<CRS>(a.A2[g], a.B2[g], a.C2[g], tc, rc.nf2, rc.nsq2, zidx, sI[2 * g],
+                                    sI[2 * g + 1], sX[2 * g], sX[2 * g + 1], sO[2 * g],
+                                    sO[2 * g + 1]);
+        } else {
+            #pragma unroll
+            for (int r = 0; r < kR; ++r)
+                intersect_one<CRS>(a.Ar[r], a.Br[r], a.Cr[r], tc, rc.nf, rc.nsq, zidx, sI[r],
+                                   sX[r], sO[r]);
+        }
+    };
+    setup(0);
+    for (int t = 0; t < ntr; ++t) {
+        int cI[kR];
+        float cX[kR];
+        #pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            cI[r] = sI[r];
+            cX[r] = sX[r];
+            a.cntv[r] += sO[r] ? 1 : 0;
+        }
+        setup(min(t + 1, ntr - 1));
+        #pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            if constexpr (CFG::kMode == kScalar) {
+                float F[W + 1];
+                #pragma unroll
+                for (int j = 0; j <= W; ++j) F[j] = smf[cI[g] + j];
+                #pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    const float v = fmaf(cX[g], F[j + 1] - F[j], F[j]);
+                    a.num1[g][j] += v;
+                    a.den1[g][j & 1] = fmaf(v, v, a.den1[g][j & 1]);
+                }
+            } else {
+                const int ra = 2 * g, rb = 2 * g + 1;
+                float FA[W + 1], FB[W + 1];
+                #pragma unroll
+                for (int j = 0; j <= W; ++j) { FA[j] = smf[cI[ra] + j]; FB[j] = smf[cI[rb] + j]; }
+                const f2_t x2 = pk2(cX[ra], cX[rb]);
+                #pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    f2_t v;
+                    if constexpr (CFG::kMode == kPacked) {
+                        v = fma2(x2, sub2(pk2(FA[j + 1], FB[j + 1]), pk2(FA[j], FB[j])),
+                                 pk2(FA[j], FB[j]));
+                    } else if constexpr (CFG::kMode == kHybridD) {
+                        v = fma2(x2, pk2(FA[j + 1] - FA[j], FB[j + 1] - FB[j]), pk2(FA[j], FB[j]));
+                    } else {
+                        v = pk2(fmaf(cX[ra], FA[j + 1] - FA[j], FA[j]),
+                                fmaf(cX[rb], FB[j + 1] - FB[j], FB[j]));
+                    }
+                    a.num2[g][j] = add2(a.num2[g][j], v);
+                    a.den2[g][j & 1] = fma2(v, v, a.den2[g][j & 1]);
+                }
+            }
+        }
+    }
+}
+
+// End a pass: Eq. 1 per candidate, S cube entries, running best (ties: lowest index, since
+// a thread meets its candidates in increasing order).
+template <int W, class CFG>
+__device__ __forceinline__ void accum_end(const Accum<W, CFG>& a, int ncand, float* S_row,
+                                          float& bestS, int& bestC, float& bestT) {
+    #pragma unroll
+    for (int r = 0; r < CFG::kR; ++r) {
+        const int c = a.cidx[r];
+        if (c >= ncand) continue;
+        // the numerator is summed in the same even/odd order as the energy, so a lone
+        // participating trace gives exactly S = 1
+        float nu0 = 0.f, nu1 = 0.f, ac = 0.f, d0, d1;
+        #pragma unroll
+        for (int j = 0; j < W; ++j) {
+            float v;
+            if constexpr (Accum<W, CFG>::kP) {
+                float lo, hi;
+                up2(a.num2[r / 2][j], lo, hi);
+                v = (r & 1) ? hi : lo;
+            } else {
+                v = a.num1[r][j];
+            }
+            if (j & 1) nu1 = fmaf(v, v, nu1); else nu0 = fmaf(v, v, nu0);
+            ac += v;
+        }
+        if constexpr (Accum<W, CFG>::kP) {
+            float l0, h0, l1, h1;
+            up2(a.den2[r / 2][0], l0, h0);
+            up2(a.den2[r / 2][1], l1, h1);
+            d0 = (r & 1) ? h0 : l0;
+            d1 = (r & 1) ? h1 : l1;
+        } else {
+            d0 = a.den1[r][0];
+            d1 = a.den1[r][1];
+        }
+        const float nu = nu0 + nu1, dn = d0 + d1;
+        const float Nf = (float)a.cntv[r];
+        const float sv = (a.cntv[r] > 0 && dn > 0.f) ? nu / (Nf * dn) : 0.f;
+        const float st = a.cntv[r] > 0 ? ac / (Nf * (float)W) : 0.f;
+        if (S_row) S_row[c] = sv;
+        if (sv > bestS) { bestS = sv; bestC = c; bestT = st; }
+    }
+}
+
+// Cross-warp argmax of the row (lane) over the nwarps consumer warps' running bests.
+__device__ __forceinline__ void reduce_best(const SearchSmem& sm, int nwarps, int lane, float& bs,
+                                            int& bc, float& bt) {
+    bs = sm.redS[0][lane];
+    bt = sm.redT[0][lane];
+    bc = sm.redC[0][lane];
+    for (int w2 = 1; w2 < nwarps; ++w2) {
+        const float sv = sm.redS[w2][lane];
+        const int c = sm.redC[w2][lane];
+        if (sv > bs || (sv == bs && c < bc)) { bs = sv; bc = c; bt = sm.redT[w2][lane]; }
+    }
+    if (bc == INT_MAX) { bc = 0; bs = 0.f; bt = 0.f; }
 }
 
 template <bool CRS, int W, class CFG>
@@ -464,26 +662,15 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
     const float* smf = reinterpret_cast<const float*>(smem_raw);
     const int zidx = (int)(reinterpret_cast<const float*>(sm.zeros) - smf);
     const bool act = n0 + lane < nrows;
-    const int n = act ? n0 + lane : (1 << 24);        // inactive rows never take part
-    const float nf = fmaxf((float)n, 1e-30f);         // > 0 keeps sqrt(n^2 + Cq) + n > 0
-    const f2_t nf2 = pk2(nf, nf);
-    const float nsq = nf * nf;
-    const f2_t nsq2 = pk2(nsq, nsq);
-    constexpr bool kP = CFG::kPairs;
-    constexpr int kG = kP ? kR / 2 : kR;             // accumulator groups per thread
-    f2_t num2[kP ? kG : 1][W];
-    f2_t den2[kP ? kG : 1][2];                       // even / odd window positions
-    float num1[kP ? 1 : kG][W];
-    float den1[kP ? 1 : kG][2];
-    int cntv[kR];
-    float Ar[kR], Br[kR], Cr[kR];
-    f2_t A2[kP ? kG : 1], B2[kP ? kG : 1], C2[kP ? kG : 1];
-    int cidx[kR];
+    const RowConst rc = row_const(act, n0 + lane);
+    const int n = rc.n;
+    Accum<W, CFG> acc;
+    #pragma unroll
+    for (int r = 0; r < kR; ++r) acc.cidx[r] = INT_MAX;
     float bestS = -1.f, bestT = 0.f;
     int bestC = INT_MAX;
     bool aborted = false;
-    #pragma unroll
-    for (int r = 0; r < kR; ++r) { cidx[r] = INT_MAX; cntv[r] = 0; Ar[r] = Br[r] = Cr[r] = 0.f; }
+    auto decode = [&](int c, float& a, float& b, float& cc) { decode_candidate<CRS>(P, c, a, b, cc); };
 
     for (int s = 0;; ++s) {
         const int slot = s % kSlots;
@@ -498,142 +685,15 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
             aborted = sm.abort_flag != 0;
             break;
         }
-        if (d.first) {
-            #pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                const int c = d.pass * kCB + warp * kR + r;
-                cidx[r] = c;
-                Ar[r] = Br[r] = Cr[r] = 0.f;   // past the end: computed, then discarded
-                if (c < P.ncand) decode_candidate<CRS>(P, c, Ar[r], Br[r], Cr[r]);
-                cntv[r] = 0;
-            }
-            #pragma unroll
-            for (int g = 0; g < kG; ++g) {
-                if constexpr (kP) {
-                    A2[g] = pk2(Ar[2 * g], Ar[2 * g + 1]);
-                    B2[g] = pk2(Br[2 * g], Br[2 * g + 1]);
-                    C2[g] = pk2(Cr[2 * g], Cr[2 * g + 1]);
-                    den2[g][0] = den2[g][1] = 0ull;
-                    #pragma unroll
-                    for (int j = 0; j < W; ++j) num2[g][j] = 0ull;
-                } else {
-                    den1[g][0] = den1[g][1] = 0.f;
-                    #pragma unroll
-                    for (int j = 0; j < W; ++j) num1[g][j] = 0.f;
-                }
-            }
-        }
+        if (d.first) accum_begin(acc, d.pass * kCB + warp * kR, P.ncand, decode);
         const int ntr = min(d.ntr, kChunkT);
         const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
         // a warp whose candidates of this pass all lie past the end skips the stage
-        if (ntr > 0 && cidx[0] < P.ncand) {
-            // Software pipeline: the traveltimes of trace t+1 (long MUFU chains) are formed
-            // while the window of trace t is accumulated.
-            int sI[kR];
-            float sX[kR];
-            bool sO[kR];
-            auto setup = [&](int t) {
-                const TraceConst tc = trace_const(sm.meta[slot][t], n, slot_base, HW);
-                if constexpr (CFG::kMode == kPacked) {
-                    #pragma unroll
-                    for (int g = 0; g < kG; ++g)
-                        intersect_pair<CRS>(A2[g], B2[g], C2[g], tc, nf2, nsq2, zidx, sI[2 * g],
-                                            sI[2 * g + 1], sX[2 * g], sX[2 * g + 1], sO[2 * g],
-                                            sO[2 * g + 1]);
-                } else {
-                    #pragma unroll
-                    for (int r = 0; r < kR; ++r)
-                        intersect_one<CRS>(Ar[r], Br[r], Cr[r], tc, nf, nsq, zidx, sI[r], sX[r], sO[r]);
-                }
-            };
-            setup(0);
-            for (int t = 0; t < ntr; ++t) {
-                int cI[kR];
-                float cX[kR];
-                #pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    cI[r] = sI[r];
-                    cX[r] = sX[r];
-                    cntv[r] += sO[r] ? 1 : 0;
-                }
-                setup(min(t + 1, ntr - 1));
-                #pragma unroll
-                for (int g = 0; g < kG; ++g) {
-                    if constexpr (CFG::kMode == kScalar) {
-                        float F[W + 1];
-                        #pragma unroll
-                        for (int j = 0; j <= W; ++j) F[j] = smf[cI[g] + j];
-                        #pragma unroll
-                        for (int j = 0; j < W; ++j) {
-                            const float v = fmaf(cX[g], F[j + 1] - F[j], F[j]);
-                            num1[g][j] += v;
-                            den1[g][j & 1] = fmaf(v, v, den1[g][j & 1]);
-                        }
-                    } else {
-                        const int ra = 2 * g, rb = 2 * g + 1;
-                        float FA[W + 1], FB[W + 1];
-                        #pragma unroll
-                        for (int j = 0; j <= W; ++j) { FA[j] = smf[cI[ra] + j]; FB[j] = smf[cI[rb] + j]; }
-                        const f2_t x2 = pk2(cX[ra], cX[rb]);
-                        #pragma unroll
-                        for (int j = 0; j < W; ++j) {
-                            f2_t v;
-                            if constexpr (CFG::kMode == kPacked) {
-                                v = fma2(x2, sub2(pk2(FA[j + 1], FB[j + 1]), pk2(FA[j], FB[j])),
-                                         pk2(FA[j], FB[j]));
-                            } else if constexpr (CFG::kMode == kHybridD) {
-                                v = fma2(x2, pk2(FA[j + 1] - FA[j], FB[j + 1] - FB[j]),
-                                         pk2(FA[j], FB[j]));
-                            } else {
-                                v = pk2(fmaf(cX[ra], FA[j + 1] - FA[j], FA[j]),
-                                        fmaf(cX[rb], FB[j + 1] - FB[j], FB[j]));
-                            }
-                            num2[g][j] = add2(num2[g][j], v);
-                            den2[g][j & 1] = fma2(v, v, den2[g][j & 1]);
-                        }
-                    }
-                }
-            }
-        }
-        if (d.last) {
-            #pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                const int c = cidx[r];
-                if (c >= P.ncand) continue;
-                // the numerator is summed in the same even/odd order as the energy, so a
-                // lone participating trace gives exactly S = 1
-                float nu0 = 0.f, nu1 = 0.f, ac = 0.f, d0, d1;
-                #pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    float a;
-                    if constexpr (kP) {
-                        float lo, hi;
-                        up2(num2[r / 2][j], lo, hi);
-                        a = (r & 1) ? hi : lo;
-                    } else {
-                        a = num1[r][j];
-                    }
-                    if (j & 1) nu1 = fmaf(a, a, nu1); else nu0 = fmaf(a, a, nu0);
-                    ac += a;
-                }
-                if constexpr (kP) {
-                    float l0, h0, l1, h1;
-                    up2(den2[r / 2][0], l0, h0);
-                    up2(den2[r / 2][1], l1, h1);
-                    d0 = (r & 1) ? h0 : l0;
-                    d1 = (r & 1) ? h1 : l1;
-                } else {
-                    d0 = den1[r][0];
-                    d1 = den1[r][1];
-                }
-                const float nu = nu0 + nu1, dn = d0 + d1;
-                const float Nf = (float)cntv[r];
-                const float sv = (cntv[r] > 0 && dn > 0.f) ? nu / (Nf * dn) : 0.f;
-                const float st = cntv[r] > 0 ? ac / (Nf * (float)W) : 0.f;
-                if (P.S_cube && act) P.S_cube[(row0 + n) * (int64_t)P.ncand + c] = sv;
-                if (sv > bestS) { bestS = sv; bestC = c; bestT = st; }
-            }
-        }
+        if (ntr > 0 && acc.cidx[0] < P.ncand)
+            accum_stage<CRS, W, CFG>(acc, sm.meta[slot], ntr, slot_base, rc, zidx, smf);
+        if (d.last)
+            accum_end(acc, P.ncand, (P.S_cube && act) ? P.S_cube + (row0 + n) * (int64_t)P.ncand
+                                                      : nullptr, bestS, bestC, bestT);
         mbar_arrive(&sm.empty[slot]);                   // this thread is done with the slot
     }
 
@@ -643,15 +703,9 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
     consumer_bar(kConsumers);
     if (aborted || sm.abort_flag) return;
     if (warp == 0 && act) {
-        float bs = sm.redS[0][lane], bt = sm.redT[0][lane];
-        int bc = sm.redC[0][lane];
-        #pragma unroll
-        for (int w2 = 1; w2 < kWarps; ++w2) {
-            const float sv = sm.redS[w2][lane];
-            const int c = sm.redC[w2][lane];
-            if (sv > bs || (sv == bs && c < bc)) { bs = sv; bc = c; bt = sm.redT[w2][lane]; }
-        }
-        if (bc == INT_MAX) { bc = 0; bs = 0.f; bt = 0.f; }
+        float bs, bt;
+        int bc;
+        reduce_best(sm, kWarps, lane, bs, bc, bt);
         const int64_t row = row0 + n;
         P.best_idx[row] = bc;
         P.best_S[row] = bs;

@@ -176,6 +176,7 @@ extern "C" int seis_device_status(void* stream) {
     if (e != cudaSuccess) return cuda_fail(e, "seis_device_status");
     if (v & kStatusTimeout) return fail(SEIS_ETIMEOUT, "a device wait timed out");
     if (v & kStatusOverflow) return fail(SEIS_EUNSUPPORTED, "a staged trace window overflowed");
+    if (v & kStatusBadItem) return fail(SEIS_EINVAL, "a batch item with an out-of-range field was skipped");
     return SEIS_OK;
 }
 

@@ -9,6 +9,7 @@ namespace seis {
 // Device status word bits (read back by seis_device_status).
 constexpr unsigned kStatusTimeout = 1u;
 constexpr unsigned kStatusOverflow = 2u;   // a staged trace window did not fit (never expected)
+constexpr unsigned kStatusBadItem = 4u;    // a batch item with an out-of-range field was skipped
 
 // One semblance search launch.  An "owner" is a CMP gather (CMP) or a central CDP (CRS);
 // each CTA handles one owner and a tile of 32 consecutive output rows of it.
@@ -86,6 +87,33 @@ cudaError_t launch_search(const SearchParams& p, bool crs, int w, cudaStream_t s
 cudaError_t launch_eval(const EvalParams& p, bool crs, bool grad, int w, cudaStream_t s);
 cudaError_t launch_refine_update(const RefineParams& r, cudaStream_t s);
 int eval_tile_rows();
+
+// Batched search: one persistent launch over items (see seis_batch_semblance).
+struct BatchParams {
+    const float* traces;
+    const int64_t* trace_off;
+    const float* h;
+    const float* m;
+    int64_t ntraces;
+    const seis_batch_item* items;
+    int64_t nitems;
+    int64_t item_begin, item_end;   // the launch serves items [item_begin, item_end)
+    const float* poolA;
+    const float* poolB;
+    const float* poolC;
+    int32_t sizeA, sizeB, sizeC;
+    int32_t* best_idx;
+    float* best_ABC;
+    float* best_S;
+    float* stack;
+    unsigned long long* counter;    // next task (device)
+    int64_t* task_off;              // [nitems + 1] first task of each item (device)
+    unsigned* status;
+    int variant;
+};
+cudaError_t launch_batch_setup(const BatchParams& p, int64_t out_rows, cudaStream_t s);
+cudaError_t launch_batch(const BatchParams& p, int w, int grid, cudaStream_t s);
+int batch_variant_of(int search_variant);
 int search_variant_count();
 const char* search_variant_name(int v);
 

@@ -80,6 +80,10 @@ def load_library(path: str | None = None):
             lib.seis_refine_workspace_size.restype = ctypes.c_size_t
             lib.crs_refine.argtypes = [vp, vp, vp, vp, vp, i32, f32, i32, vp, vp, vp, vp,
                                        ctypes.c_size_t, i64, vp]
+            lib.seis_batch_workspace_size.argtypes = [i64]
+            lib.seis_batch_workspace_size.restype = ctypes.c_size_t
+            lib.seis_batch_semblance.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, i32,
+                                                 vp, vp, vp, vp, i64, vp, ctypes.c_size_t, vp]
             lib.seis_autotune_save.argtypes = [ctypes.c_char_p]
             lib.seis_autotune_load.argtypes = [ctypes.c_char_p]
             for name in ("seis_device_status", "cmp_semblance", "crs_semblance",
@@ -87,7 +91,7 @@ def load_library(path: str | None = None):
                          "seis_set_search_variant", "seis_get_search_variant",
                          "seis_autotune_cmp", "seis_autotune_crs", "seis_autotune_save",
                          "seis_autotune_load", "seis_autotune_clear", "stack",
-                         "crs_semblance_grad", "crs_refine"):
+                         "crs_semblance_grad", "crs_refine", "seis_batch_semblance"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -391,6 +395,50 @@ class CRSSemblance(torch.autograd.Function):
 def crs_semblance_at(ABC: torch.Tensor, g: Gathers, ap: "Aperture", w: int = 11):
     """Differentiable semblance of one CRS operator per row (see CRSSemblance)."""
     return CRSSemblance.apply(ABC, g, ap, w)
+
+
+@dataclass
+class Batch:
+    """Batched items resident on the GPU (include/seis.h: seis_batch_item)."""
+    items: torch.Tensor            # uint8 [nitems * 64], the raw item table
+    nitems: int
+    poolA: torch.Tensor
+    poolB: torch.Tensor
+    poolC: torch.Tensor
+    out_rows: int
+    workspace: torch.Tensor
+
+
+def batch_to_device(items: np.ndarray, poolA, poolB, poolC, out_rows: int, device="cuda") -> Batch:
+    """Copy a structured item array (synth.BATCH_ITEM_DTYPE) and the candidate pools."""
+    lib = load_library()
+    raw = torch.from_numpy(np.ascontiguousarray(items).view(np.uint8).copy()).to(device)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+    nbytes = lib.seis_batch_workspace_size(len(items))
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    return Batch(raw, len(items), f(poolA), f(poolB), f(poolC), int(out_rows), ws)
+
+
+def batch_semblance(g: Gathers, b: Batch, w: int = 11, mode: int = 0, stream=None,
+                    out: dict | None = None) -> dict:
+    """Batched search over uneven CMP / CRS items (include/seis.h: seis_batch_semblance);
+    mode 0 = one persistent launch, 1 = one launch per item."""
+    lib = load_library()
+    dev = g.traces.device
+    if out is None:
+        out = dict(best_idx=torch.empty(b.out_rows, dtype=torch.int32, device=dev),
+                   best_ABC=torch.empty((b.out_rows, 3), dtype=torch.float32, device=dev),
+                   best_S=torch.empty(b.out_rows, dtype=torch.float32, device=dev),
+                   stack=torch.empty(b.out_rows, dtype=torch.float32, device=dev))
+    base = b.workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    _check(lib.seis_batch_semblance(
+        ctypes.byref(g.descriptor()), _ptr(b.items), b.nitems, _ptr(b.poolA), int(b.poolA.numel()),
+        _ptr(b.poolB), int(b.poolB.numel()), _ptr(b.poolC), int(b.poolC.numel()), w, mode,
+        _ptr(out["best_idx"]), _ptr(out["best_ABC"]), _ptr(out["best_S"]), _ptr(out["stack"]),
+        b.out_rows, ctypes.c_void_p(aligned), b.workspace.numel() - (aligned - base),
+        _stream_handle(stream)))
+    return out
 
 
 def device_status(stream=None) -> None:

@@ -228,3 +228,94 @@ def crs_ranges(max_dip_deg=20.0, vmin=1500.0, vlo=1400.0, vhi=4500.0):
     cmax = 4.0 / vlo ** 2
     cmin = 4.0 / vhi ** 2
     return (-amax, amax), (-cmax, cmax), (cmin, cmax)
+
+
+# --- batched uneven items --------------------------------------------------------------
+
+# numpy mirror of the seis_batch_item layout (64 bytes; field order and types as in the C ABI)
+BATCH_ITEM_DTYPE = np.dtype([("trace_begin", "<i8"), ("trace_end", "<i8"), ("out_begin", "<i8"),
+                             ("rows", "<i4"), ("kind", "<i4"), ("dt", "<f4"), ("m_c", "<f4"),
+                             ("a_off", "<i4"), ("nA", "<i4"), ("b_off", "<i4"), ("nB", "<i4"),
+                             ("c_off", "<i4"), ("nC", "<i4")])
+
+
+def batch_workload(n_items=10000, seed=4, fold=(8, 120), ns=(1000, 4000), dts=(0.002, 0.004),
+                   nc_range=(101, 201), crs_grid=(11, 11, 21), p_crs=0.5, snr=2.0,
+                   max_dm=125.0, hmax=2500.0):
+    """Uneven items: each a CMP gather (prob 1 - p_crs) or a CRS supergather whose traces
+    carry their own midpoint offsets dm ~ U(-max_dm, max_dm).  Fold ~ U{fold}, samples ~
+    U{ns}, dt from dts.  CMP items search nc ~ U{nc_range} values of C = 4/v^2 (v in
+    1400..4500 m/s); CRS items the crs_grid over crs_ranges().  Events: dipping planes
+    through the item centre (exact CRS form) and, for CMP items, hyperbolae.  Items come out
+    sorted by cost per 32-row task (fold x candidates), largest first.
+    Returns (dataset dict, items structured array, poolA, poolB, poolC)."""
+    rng = np.random.default_rng(seed)
+    (alo, ahi), (blo, bhi), (clo, chi) = crs_ranges()
+    poolA = np.linspace(alo, ahi, crs_grid[0]).astype(np.float32)
+    poolB = np.linspace(blo, bhi, crs_grid[1]).astype(np.float32)
+    cmp_grids = {nc: (4.0 / np.linspace(1400.0, 4500.0, nc) ** 2).astype(np.float32)
+                 for nc in range(nc_range[0], nc_range[1] + 1)}
+    pieces = [np.linspace(clo, chi, crs_grid[2]).astype(np.float32)]
+    c_off_of = {}
+    off = crs_grid[2]
+    for nc, gvals in cmp_grids.items():
+        c_off_of[nc] = off
+        pieces.append(gvals)
+        off += nc
+    poolC = np.concatenate(pieces)
+    kinds = (rng.random(n_items) < p_crs).astype(np.int32)
+    folds = rng.integers(fold[0], fold[1] + 1, n_items)
+    nss = rng.integers(ns[0], ns[1] + 1, n_items)
+    dtv = np.asarray(dts, np.float64)[rng.integers(0, len(dts), n_items)]
+    ncs = rng.integers(nc_range[0], nc_range[1] + 1, n_items)
+    cost = folds * np.where(kinds == 1, int(np.prod(crs_grid)), ncs)
+    order = np.argsort(-cost, kind="stable")
+    kinds, folds, nss, dtv, ncs = kinds[order], folds[order], nss[order], dtv[order], ncs[order]
+    trace_off = [0]
+    traces, hs, ms = [], [], []
+    items = np.zeros(n_items, BATCH_ITEM_DTYPE)
+    tb = 0
+    ob = 0
+    for i in range(n_items):
+        M, L, dt, kind = int(folds[i]), int(nss[i]), float(dtv[i]), int(kinds[i])
+        T = L * dt
+        mcen = 1000.0 * i
+        h = rng.uniform(0.0, hmax, M)
+        dm = rng.uniform(-max_dm, max_dm, M) if kind else np.zeros(M)
+        blk = np.zeros((M, L))
+        times, amps = [], []
+        for _ in range(int(rng.integers(2, 5))):
+            v = rng.uniform(1500.0, 4000.0)
+            a = np.deg2rad(rng.uniform(-20.0, 20.0)) if kind else 0.0
+            t0 = rng.uniform(0.2, 0.85 * T)
+            p = t0 + 2.0 * np.sin(a) * dm / v
+            t = np.where(p > 0, np.sqrt(np.maximum(p, 0) ** 2 + 4.0 * np.cos(a) ** 2 * h ** 2 / v ** 2),
+                         np.nan)
+            times.append(t)
+            amps.append(np.full(M, rng.uniform(0.5, 1.0) * rng.choice([-1.0, 1.0])))
+        _add_events_uniform(blk, np.array(times), np.array(amps), dt)
+        if snr:
+            sig = _noise_sigma(blk.reshape(1, -1), snr)[0]
+            blk += np.random.default_rng([seed, 7, i]).standard_normal(blk.shape) * sig
+        traces.append(blk.astype(np.float32).reshape(-1))
+        trace_off.extend(list(trace_off[-1] + L * np.arange(1, M + 1)))
+        hs.append(h.astype(np.float32))
+        ms.append((mcen + dm).astype(np.float32))
+        it = items[i]
+        it["trace_begin"], it["trace_end"] = tb, tb + M
+        it["out_begin"], it["rows"], it["kind"] = ob, L, kind
+        it["dt"], it["m_c"] = dt, mcen
+        if kind:
+            it["a_off"], it["nA"], it["b_off"], it["nB"] = 0, crs_grid[0], 0, crs_grid[1]
+            it["c_off"], it["nC"] = 0, crs_grid[2]
+        else:
+            it["a_off"], it["nA"], it["b_off"], it["nB"] = 0, 1, 0, 1
+            it["c_off"], it["nC"] = c_off_of[int(ncs[i])], int(ncs[i])
+        tb += M
+        ob += L
+    ntr = tb
+    ds = dict(traces=np.concatenate(traces), trace_off=np.asarray(trace_off, np.int64),
+              h=np.concatenate(hs), m=np.concatenate(ms),
+              gather_off=np.array([0, ntr], np.int64), out_off=np.array([0, ob], np.int64),
+              dt=np.float32([dtv[0]]), out_rows=ob)
+    return ds, items, poolA, poolB, poolC
