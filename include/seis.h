@@ -236,6 +236,29 @@ int seis_batch_semblance(const seis_gathers* d, const seis_batch_item* items, in
                          int32_t* best_idx, float* best_ABC, float* best_S, float* stack_out,
                          int64_t out_rows, void* workspace, size_t ws_bytes, void* stream);
 
+/* Allocation-free batched search (the paper has no counterpart: it concerns how this
+ * library is called, not the method).  For callers that cannot allocate device memory
+ * where they call the library -- a service running under a fixed device-memory budget, a
+ * plug-in whose host application owns all allocations, a latency-bound loop that cannot
+ * afford cudaMalloc's possible device synchronisation -- this runs seis_batch_semblance in
+ * its persistent mode (mode 0) with the scratch (work counter and task table) kept in a
+ * device array inside the library instead of a caller workspace.  Limits and behaviour:
+ *   - at most SEIS_NOALLOC_MAX_ITEMS items per call (SEIS_EINVAL beyond); the array,
+ *     256 + 8 * (SEIS_NOALLOC_MAX_ITEMS + 1) bytes (about 512 KiB), is held on every GPU
+ *     that loads the library until the process exits;
+ *   - the first call on a device looks the array's device address up (a runtime query,
+ *     not an allocation), so make that first call before any stream capture;
+ *   - every call shares the array (each rebuilds the task table and zeroes the counter):
+ *     calls whose work overlaps on the GPU race on it, so serialise them;
+ *   - nothing is allocated: no cudaMalloc, no cudaFree, no allocating library routine.
+ * Arguments and results as seis_batch_semblance. */
+#define SEIS_NOALLOC_MAX_ITEMS 65536
+int seis_batch_semblance_noalloc(const seis_gathers* d, const seis_batch_item* items,
+                                 int64_t nitems, const float* poolA, int32_t sizeA,
+                                 const float* poolB, int32_t sizeB, const float* poolC,
+                                 int32_t sizeC, int32_t w, int32_t* best_idx, float* best_ABC,
+                                 float* best_S, float* stack_out, int64_t out_rows, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
