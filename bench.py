@@ -1,17 +1,24 @@
 #!/usr/bin/env python3
-"""Benchmark of the CMP semblance search on GB300 (one JSON line on rank 0).
+"""Benchmark of the semblance search on GB300 (one JSON line on rank 0).
 
-Workload (default): a 2-D line of 4096 CMP gathers, fold 60, half-offsets 25..3000 m,
-2000 samples at 4 ms, 8 hyperbolic events with a lateral velocity gradient, SNR 1;
-201 candidates C = 4/v^2 for v in 1400..4500 m/s; window w = 11.  One step = one
+Default workload (cmp-line): a 2-D line of 4096 CMP gathers, fold 60, half-offsets
+25..3000 m, 2000 samples at 4 ms, 8 hyperbolic events with a lateral velocity gradient,
+SNR 1; 201 candidates C = 4/v^2 for v in 1400..4500 m/s; window w = 11.  One step = one
 cmp_semblance call over all gathers (the whole hot path: traveltime, interpolation,
 semblance, argmax, stack).  The metric is interpolated trace-samples per second
 (intersections x w / s); an intersection is one (gather, t0, candidate, trace) visit.
+Before the timed region the autotuner picks the kernel variant on a 512-gather slice of
+the same shape bucket.
 
---impl reference times the FP64 CPU oracle on the host cores on a bounded sample of
-the same workload (the reference arm of this build: the paper publishes no code).
-Under torchrun (N > 1) every rank processes its own line of 4096 gathers (weak
-scaling, no collective on the data path); rank 0 prints the line.
+Other workloads (--workload): crs-line (1024 central CMPs, aperture +-10 CMPs, fold 48,
+21x21x41 grid; --centrals limits the centrals), batch (10,000 uneven CMP/CRS items in one
+persistent launch; --items), refine (512 central CMPs, coarse 7x7x11 search + 20
+gradient-ascent steps, against the dense 41x41x81 search on --dense-centrals centrals).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
+same workload (the reference arm of this build: the paper publishes no code).  Under
+torchrun (N > 1) every rank processes its own line (weak scaling, no collective on the
+data path); rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -36,6 +43,7 @@ VMIN, VMAX = 1400.0, 4500.0
 FLOPS_PER_INTERSECTION = 12 + 7 * W        # the paper's count (Eq. 2)
 SM_MAX_MHZ = 2070.0
 WORKLOAD = "cmp-line: 4096 gathers x fold 60 x 2000 samples @4ms, 201 C candidates, w=11"
+METRIC = "semblance interpolated trace-samples/s"
 
 
 def _env_rank():
@@ -123,7 +131,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
@@ -132,6 +140,7 @@ class ClockSampler:
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, f[5:9]):
@@ -141,11 +150,12 @@ class ClockSampler:
         if not sm:
             return None
         return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)),
-                    samples=len(sm), reasons=sorted(reasons))
+                    power_w_median=float(np.median(pw)), samples=len(sm),
+                    reasons=sorted(reasons))
 
 
 def _profile_traffic(kernel_tag):
-    """DRAM traffic per launch from a committed ncu summary, if it was taken on the
+    """DRAM traffic per unit (gather) from a committed ncu summary, if it was taken on the
     current kernel source (hash match); else None."""
     src = sorted(glob.glob(os.path.join(ROOT, "paper_1907_11678_gb300", "csrc", "*")))
     h = hashlib.sha256()
@@ -161,26 +171,45 @@ def _profile_traffic(kernel_tag):
         return None, digest
     if d.get("csrc_sha256_16") != digest:
         return None, digest
-    return d.get("dram_bytes_per_launch"), digest
+    return d.get("dram_bytes_per_gather"), digest
 
 
-def run_ours(args):
-    import torch
-    import torch.distributed as dist
-    from paper_1907_11678_gb300 import build as seis_build
-    from paper_1907_11678_gb300 import seis, synth
+def _time_steps(torch, stream, fn, steps):
+    """Per-step and total CUDA-event times (ms) of `steps` calls of fn on `stream`."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], t0.elapsed_time(t1)
 
-    rank, world, local = _env_rank()
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", torch.cuda.current_device())
-    seis_build.build()
+
+def _max_over_ranks(torch, dist, world, dev, x):
+    if world <= 1:
+        return x
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ the cmp-line workload --
+
+def run_cmp_line(args, torch, dist, seis, synth, rank, world, dev):
     ds = synth.workload_cmp_line(seed=2 + 1000 * rank, G=args.gathers)
     C = _candidates()
     inter = _intersections(ds, NC)
     g = seis.to_device(ds, dev)
     Cd = torch.from_numpy(C).to(dev)
+    # autotune on a slice in the same shape bucket (same fold, rows, candidates)
+    sub = synth.cmp_line(min(512, args.gathers), 60, 2000, 0.004, 25.0, 3000.0, 8, 1.0,
+                         seed=99, v_range=(2550.0, 3450.0), v_gradient=0.5)
+    chosen, tune_ms = seis.autotune_cmp(seis.to_device(sub, dev), Cd, w=W, reps=2)
     out = seis.cmp_semblance(g, Cd, w=W)              # allocate outputs once
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -188,120 +217,35 @@ def run_ours(args):
     torch.cuda.synchronize()
     seis.device_status()
 
-    # ---- device-resident timing (CUDA events on the launching stream) -----------------
     clocks = ClockSampler(dev.index)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for i in range(args.steps):
-        ev[i][0].record(stream)
-        seis.cmp_semblance(g, Cd, w=W, out=out)
-        ev[i][1].record(stream)
-    t1.record(stream)
-    torch.cuda.synchronize()
+    kern_ms, total_ms = _time_steps(torch, stream, lambda: seis.cmp_semblance(g, Cd, w=W, out=out),
+                                    args.steps)
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    total_ms = t0.elapsed_time(t1)
-    kern_ms = [a.elapsed_time(b) for a, b in ev]
     seis.device_status()
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = _max_over_ranks(torch, dist, world, dev, total_ms)
     ms_per_step = total_ms / args.steps
-    value = inter * world * W / (ms_per_step / 1e3)
 
-    # ---- end to end through the C ABI with host buffers ----------------------------------
-    e2e = None
-    if not args.skip_e2e:
-        e2e = _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream)
-    line = _line(args, ds, g, inter, world, ms_per_step, value, kern_ms, clk, e2e, dev)
-    if rank == 0 and not args.no_cpu_baseline:
-        v, info = oracle_baseline(ds, C, target_s=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "trace-samples/s", "cores": info["cores"],
-                                "kind": "oracle", "sample": info["sample"],
-                                "cpu": info["cpu"], "seconds": info["seconds"]}
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-
-
-def _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream):
-    """Same metric through the C ABI with the step's inputs copied from pinned host
-    memory and its results copied back inside the timed region."""
-    import torch as _t
-    import torch.distributed as dist
-    from paper_1907_11678_gb300 import seis
-    host = {k: _t.from_numpy(np.ascontiguousarray(ds[k])).pin_memory()
-            for k in ("traces", "trace_off", "h", "gather_off", "out_off", "dt")}
-    dev_bufs = {k: _t.empty_like(v, device=dev) for k, v in host.items()}
-    Ch = _t.from_numpy(C).pin_memory()
-    outs_h = {k: _t.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
-    h2d = sum(v.numel() * v.element_size() for v in host.values()) + Ch.numel() * 4
-    d2h = sum(v.numel() * v.element_size() for v in out.values())
-    g2 = seis.Gathers(traces=dev_bufs["traces"], trace_off=dev_bufs["trace_off"],
-                      h=dev_bufs["h"], m=None, gather_off=dev_bufs["gather_off"],
-                      out_off=dev_bufs["out_off"], dt=dev_bufs["dt"], ngathers=g.ngathers,
-                      ntraces=g.ntraces, max_rows=g.max_rows,
-                      max_trace_samples=g.max_trace_samples, rows=g.rows)
-    Cd2 = _t.empty_like(Cd)
-
-    def e2e_step():
-        for k in host:
-            dev_bufs[k].copy_(host[k], non_blocking=True)
-        Cd2.copy_(Ch, non_blocking=True)
-        seis.cmp_semblance(g2, Cd2, w=W, out=out)
-        for k in out:
-            outs_h[k].copy_(out[k], non_blocking=True)
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    _t.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    e0 = _t.cuda.Event(enable_timing=True)
-    e1 = _t.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    _t.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    # results of the e2e path equal the device-resident ones
-    assert np.array_equal(outs_h["best_idx"].numpy(), out["best_idx"].cpu().numpy())
-    return {"value": inter * world * W / (e2e_ms / 1e3), "unit": "trace-samples/s",
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": e2e_ms}
-
-
-def _line(args, ds, g, inter, world, ms_per_step, value, kern_ms, clk, e2e, dev):
-    import torch
+    e2e = None if args.skip_e2e else _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream,
+                                          torch, dist, seis)
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peak_tflops = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
     avg_kernel_s = float(np.mean(kern_ms)) / 1e3
     achieved = inter * FLOPS_PER_INTERSECTION / avg_kernel_s / 1e12
-    traffic, digest = _profile_traffic("search_kernel_cmp_line")
-    if traffic is not None:
-        traffic = traffic * g.ngathers / 4096.0
+    tper, digest = _profile_traffic("search_kernel_cmp_line")
+    traffic = None if tper is None else tper * g.ngathers
     workload = WORKLOAD if g.ngathers == 4096 else \
         WORKLOAD.replace("4096 gathers", f"{g.ngathers} gathers (profiling size)")
-    return {
-        "metric": "CMP semblance interpolated trace-samples/s",
-        "value": value,
+    line = {
+        "metric": "CMP " + METRIC,
+        "value": inter * world * W / (ms_per_step / 1e3),
         "unit": "trace-samples/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -316,18 +260,233 @@ def _line(args, ds, g, inter, world, ms_per_step, value, kern_ms, clk, e2e, dev)
                    "samples": 2000, "candidates": NC, "w": W,
                    "intersections_per_step": inter * world,
                    "l2": "inputs larger than L2 (1.97 GB of traces per GPU)",
-                   "parallelism": f"gathers sharded, dp{world}" if world > 1 else "1 GPU"},
+                   "parallelism": f"gathers sharded, dp{world}" if world > 1 else "1 GPU",
+                   "kernel_variant": chosen,
+                   "kernel_variant_name": seis.search_variants()[chosen],
+                   "autotune_ms_512_gathers": [round(x, 3) for x in tune_ms]},
         "intersections_per_s": inter * world / (ms_per_step / 1e3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": traffic,
+                     "algorithmic_bytes": int(ds["traces"].nbytes + ds["h"].nbytes
+                                              + 4 * 4 * int(ds["out_off"][-1])),
                      "flops_per_intersection": FLOPS_PER_INTERSECTION,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
-                     "kernel": "search_kernel<CMP, w=11>", "csrc_sha256_16": digest},
+                     "kernel": f"search_kernel<CMP, w=11, variant {chosen}>",
+                     "csrc_sha256_16": digest},
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, info = oracle_baseline(ds, C, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "trace-samples/s", "cores": info["cores"],
+                                "kind": "oracle", "sample": info["sample"],
+                                "cpu": info["cpu"], "seconds": info["seconds"]}
+    return line
+
+
+def _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream, torch, dist, seis):
+    """Same metric through the C ABI with the step's inputs copied from pinned host
+    memory and its results copied back inside the timed region."""
+    host = {k: torch.from_numpy(np.ascontiguousarray(ds[k])).pin_memory()
+            for k in ("traces", "trace_off", "h", "gather_off", "out_off", "dt")}
+    dev_bufs = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    Ch = torch.from_numpy(C).pin_memory()
+    outs_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + Ch.numel() * 4
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    g2 = seis.Gathers(traces=dev_bufs["traces"], trace_off=dev_bufs["trace_off"],
+                      h=dev_bufs["h"], m=None, gather_off=dev_bufs["gather_off"],
+                      out_off=dev_bufs["out_off"], dt=dev_bufs["dt"], ngathers=g.ngathers,
+                      ntraces=g.ntraces, max_rows=g.max_rows,
+                      max_trace_samples=g.max_trace_samples, rows=g.rows)
+    Cd2 = torch.empty_like(Cd)
+
+    def e2e_step():
+        for k in host:
+            dev_bufs[k].copy_(host[k], non_blocking=True)
+        Cd2.copy_(Ch, non_blocking=True)
+        seis.cmp_semblance(g2, Cd2, w=W, out=out)
+        for k in out:
+            outs_h[k].copy_(out[k], non_blocking=True)
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    _, total = _time_steps(torch, stream, e2e_step, args.steps)
+    e2e_ms = _max_over_ranks(torch, dist, world, dev, total / args.steps)
+    assert np.array_equal(outs_h["best_idx"].numpy(), out["best_idx"].cpu().numpy())
+    return {"value": inter * world * W / (e2e_ms / 1e3), "unit": "trace-samples/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": e2e_ms}
+
+
+# ------------------------------------------------------------------ the other workloads ----
+
+def _crs_grids(torch, dev, synth, nA, nB, nC):
+    (alo, ahi), (blo, bhi), (clo, chi) = synth.crs_ranges()
+    f = lambda lo, hi, n: torch.from_numpy(np.linspace(lo, hi, n).astype(np.float32)).to(dev)
+    return f(alo, ahi, nA), f(blo, bhi, nB), f(clo, chi, nC)
+
+
+def _simple_line(metric, value, ms, args, world, config, extra=None, clk=None, launches=None):
+    d = {"metric": metric, "value": value, "unit": "trace-samples/s", "n_gpus": world,
+         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+         "config": config, "e2e": None, "gpu_launches": launches, "clocks": clk}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
+    ds = synth.workload_crs_line(seed=3 + 1000 * rank)
+    g = seis.to_device(ds, dev)
+    central = ds["central"][:args.centrals]
+    ap = seis.crs_aperture(g, central, ds["apm"])
+    A, B, C = _crs_grids(torch, dev, synth, 21, 21, 41)
+    inter = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 1500 * 21 * 21 * 41
+    seis.crs_semblance(g, ap, A, B, C, w=W)
+    for _ in range(args.warmup - 1):
+        seis.crs_semblance(g, ap, A, B, C, w=W)
+    torch.cuda.synchronize()
+    seis.device_status()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    kern, total = _time_steps(torch, torch.cuda.current_stream(),
+                              lambda: seis.crs_semblance(g, ap, A, B, C, w=W), args.steps)
+    clk = clocks.stop()
+    ms = _max_over_ranks(torch, dist, world, dev, total / args.steps)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    ach = inter * FLOPS_PER_INTERSECTION / (np.mean(kern) / 1e3) / 1e12
+    return _simple_line("CRS " + METRIC, inter * world * W / (ms / 1e3), ms, args, world,
+                        {"workload": f"crs-line: {len(central)} central CMPs of 1024, aperture "
+                                     "+-10 CMPs (1008 traces), 1500 samples @4ms, 21x21x41, w=11",
+                         "intersections_per_step": inter * world},
+                        {"intersections_per_s": inter * world / (ms / 1e3),
+                         "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
+                                      "unit": "TFLOP/s", "frac": ach / peak, "traffic": None}},
+                        clk, args.steps)
+
+
+def run_batch(args, torch, dist, seis, synth, rank, world, dev):
+    ds, items, A, B, C = synth.batch_workload(n_items=args.items, seed=4 + 1000 * rank)
+    g = seis.to_device(ds, dev)
+    b = seis.batch_to_device(items, A, B, C, ds["out_rows"], dev)
+    ncand = np.where(items["kind"] == 1, items["nA"] * items["nB"] * items["nC"], items["nC"])
+    inter = int(np.sum((items["trace_end"] - items["trace_begin"]) * items["rows"].astype(np.int64)
+                       * ncand))
+    out = seis.batch_semblance(g, b, w=W, mode=0)
+    torch.cuda.synchronize()
+    seis.device_status()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        seis.batch_semblance(g, b, w=W, mode=0, out=out)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    _, total = _time_steps(torch, torch.cuda.current_stream(), graph.replay, args.steps)
+    clk = clocks.stop()
+    ms = _max_over_ranks(torch, dist, world, dev, total / args.steps)
+    # the comparison: one launch per item (same kernel, one step, host wall clock)
+    t0 = time.perf_counter()
+    seis.batch_semblance(g, b, w=W, mode=1, out=out)
+    torch.cuda.synchronize()
+    per_item_ms = (time.perf_counter() - t0) * 1e3
+    seis.device_status()
+    return _simple_line("batched CMP+CRS " + METRIC, inter * world * W / (ms / 1e3), ms, args,
+                        world,
+                        {"workload": f"batch: {args.items} items (CMP p=0.5: 101-201 C; CRS "
+                                     "11x11x21), fold 8-120, 1000-4000 samples @2/4 ms, w=11, "
+                                     "one persistent launch in a CUDA graph",
+                         "intersections_per_step": inter * world},
+                        {"intersections_per_s": inter * world / (ms / 1e3),
+                         "one_launch_per_item_ms": per_item_ms,
+                         "speedup_vs_one_launch_per_item": per_item_ms / ms},
+                        clk, args.steps)
+
+
+def run_refine(args, torch, dist, seis, synth, rank, world, dev):
+    ds = synth.workload_crs_refine(seed=5 + 1000 * rank)
+    g = seis.to_device(ds, dev)
+    ap = seis.crs_aperture(g, ds["central"], ds["apm"])
+    (alo, ahi), (blo, bhi), (clo, chi) = synth.crs_ranges()
+    lo, hi = [alo, blo, clo], [ahi, bhi, chi]
+    A7, B7, C11 = _crs_grids(torch, dev, synth, 7, 7, 11)
+
+    def refine_all():
+        coarse = seis.crs_semblance(g, ap, A7, B7, C11, w=W)
+        return coarse, seis.crs_refine(g, ap, coarse["best_ABC"], lo, hi, steps=20, step0=0.05,
+                                       w=W)
+    for _ in range(args.warmup):
+        refine_all()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    _, total = _time_steps(torch, torch.cuda.current_stream(), refine_all, args.steps)
+    clk = clocks.stop()
+    refine_ms = total / args.steps
+    coarse, ref = refine_all()
+    # the dense 41x41x81 search on a slice of centrals, timed and extrapolated
+    nd = args.dense_centrals
+    apd = seis.crs_aperture(g, ds["central"][:nd], ds["apm"])
+    A41, B41, C81 = _crs_grids(torch, dev, synth, 41, 41, 81)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    dense = seis.crs_semblance(g, apd, A41, B41, C81, w=W)
+    e1.record()
+    torch.cuda.synchronize()
+    seis.device_status()
+    dense_ms_slice = e0.elapsed_time(e1)
+    dense_ms = dense_ms_slice * len(ds["central"]) / nd
+    rows_d = apd.rows
+    S_ref = ref["S"][:rows_d].cpu().numpy()
+    S_dense = dense["best_S"].cpu().numpy()
+    gap = S_dense - S_ref
+    inter_refine = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 2000 * (539 + 21)
+    return _simple_line("CRS refine " + METRIC, inter_refine * W / (refine_ms / 1e3), refine_ms,
+                        args, world,
+                        {"workload": "refine: 512 central CMPs, aperture +-8 CMPs (816 traces), "
+                                     "2000 samples @4ms; coarse 7x7x11 + 20 gradient-ascent steps "
+                                     "vs dense 41x41x81",
+                         "dense_centrals_timed": nd},
+                        {"refine_ms": refine_ms, "dense_ms_extrapolated": dense_ms,
+                         "dense_ms_slice": dense_ms_slice,
+                         "speedup_refine_vs_dense": dense_ms / refine_ms,
+                         "rows_within_1e-3_of_dense": float(np.mean(gap <= 1e-3)),
+                         "rows_above_dense": float(np.mean(gap < 0)),
+                         "median_S_refined_minus_dense": float(np.median(-gap)),
+                         "mean_S_gain_over_coarse": float((ref["S"] - coarse["best_S"]).mean())},
+                        clk, None)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1907_11678_gb300 import build as seis_build
+    from paper_1907_11678_gb300 import seis, synth
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seis_build.build()
+    fn = {"cmp-line": run_cmp_line, "crs-line": run_crs_line, "batch": run_batch,
+          "refine": run_refine}[args.workload]
+    line = fn(args, torch, dist, seis, synth, rank, world, dev)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -347,13 +506,13 @@ def run_reference(args):
     inter_per_row = NC * 60
     line = {
         "impl": "reference",
-        "metric": "CMP semblance interpolated trace-samples/s",
+        "metric": "CMP " + METRIC,
         "value": value,
         "unit": "trace-samples/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": 1e3 * 2000 * inter_per_row * W / value,
+        "ms_per_step": 1e3 * 4096 * 2000 * inter_per_row * W / value,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -376,11 +535,16 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cmp-line",
+                    choices=["cmp-line", "crs-line", "batch", "refine"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--gathers", type=int, default=4096,
                     help="gathers per GPU (4096 = the benchmark workload; fewer only for profiling)")
+    ap.add_argument("--centrals", type=int, default=1024, help="crs-line: central CMPs")
+    ap.add_argument("--items", type=int, default=10000, help="batch: items")
+    ap.add_argument("--dense-centrals", type=int, default=16, help="refine: dense-grid slice")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
     args = ap.parse_args()
     if args.impl == "reference":
