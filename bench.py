@@ -207,9 +207,14 @@ def run_cmp_line(args, torch, dist, seis, synth, rank, world, dev):
     g = seis.to_device(ds, dev)
     Cd = torch.from_numpy(C).to(dev)
     # autotune on a slice in the same shape bucket (same fold, rows, candidates)
-    sub = synth.cmp_line(min(512, args.gathers), 60, 2000, 0.004, 25.0, 3000.0, 8, 1.0,
-                         seed=99, v_range=(2550.0, 3450.0), v_gradient=0.5)
-    chosen, tune_ms = seis.autotune_cmp(seis.to_device(sub, dev), Cd, w=W, reps=2)
+    if args.variant is None:
+        sub = synth.cmp_line(min(512, args.gathers), 60, 2000, 0.004, 25.0, 3000.0, 8, 1.0,
+                             seed=99, v_range=(2550.0, 3450.0), v_gradient=0.5)
+        chosen, tune_ms = seis.autotune_cmp(seis.to_device(sub, dev), Cd, w=W, reps=2)
+    else:                                             # fixed variant (profiling runs)
+        seis.autotune_clear()
+        seis.set_search_variant(args.variant)
+        chosen, tune_ms = args.variant, []
     out = seis.cmp_semblance(g, Cd, w=W)              # allocate outputs once
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -546,6 +551,8 @@ def main():
     ap.add_argument("--items", type=int, default=10000, help="batch: items")
     ap.add_argument("--dense-centrals", type=int, default=16, help="refine: dense-grid slice")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="force a search kernel variant instead of autotuning (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
