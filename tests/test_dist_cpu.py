@@ -1,0 +1,94 @@
+"""Multi-rank decomposition on CPU (gloo, world size 2 and 3): CMP sharding covers every
+gather once; the CRS halo exchange gives every rank exactly the traces its central CDPs'
+apertures need, so its results on its own centrals equal the single-process ones."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from paper_1907_11678_gb300 import dist as sdist
+
+
+def test_shard_range_covers_everything():
+    for n in (1, 7, 4096, 10001):
+        for world in (1, 2, 3, 8):
+            ranges = [sdist.shard_range(n, world, r) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == n
+            for (a, b), (c, d) in zip(ranges, ranges[1:]):
+                assert b == c and b - a >= d - c
+            sizes = [b - a for a, b in ranges]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def test_crs_partition_halo():
+    assert sdist.crs_partition(100, 4, 0, 10) == ((0, 25), (0, 35))
+    assert sdist.crs_partition(100, 4, 1, 10) == ((25, 50), (15, 60))
+    assert sdist.crs_partition(100, 4, 3, 10) == ((75, 100), (65, 100))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    import oracle
+    from paper_1907_11678_gb300 import synth
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n_cdp, halo = 24, 3
+        full = synth.crs_line(n_cdp, 6, 260, 0.004, 0.0, 1200.0, 2, 1, 2.0, seed=17)
+        (ob, oe), (nb, ne) = sdist.crs_partition(n_cdp, world, rank, halo)
+        # this rank's owned gathers only
+        t0, t1 = int(full["gather_off"][ob]), int(full["gather_off"][oe])
+        s0, s1 = int(full["trace_off"][t0]), int(full["trace_off"][t1])
+        local = dict(traces=full["traces"][s0:s1], trace_off=full["trace_off"][t0:t1 + 1] - s0,
+                     h=full["h"][t0:t1], m=full["m"][t0:t1],
+                     gather_off=full["gather_off"][ob:oe + 1] - t0,
+                     out_off=full["out_off"][ob:oe + 1] - full["out_off"][ob],
+                     dt=full["dt"][ob:oe])
+        ext = sdist.exchange_halos(local, n_cdp, halo, rank, world)
+        assert len(ext["gather_off"]) - 1 == ne - nb
+        apm = halo * 12.5
+        A = np.float32([-2e-4, 0.0, 2e-4]); B = np.float32([0.0, 1e-6]); C = np.float32([3e-7, 8e-7, 1.5e-6])
+        central_local = np.arange(ob - nb, oe - nb, dtype=np.int32)
+        off, tr, mc = oracle.neighbours(ext, central_local, apm)
+        nb_loc = (off, tr, mc, np.arange(len(central_local) + 1, dtype=np.int64) * 260,
+                  np.float32([0.004] * len(central_local)))
+        mine = oracle.crs_semblance(ext, nb_loc, A, B, C, want_cube=True)
+        # single-process reference for the same centrals
+        off2, tr2, mc2 = oracle.neighbours(full, np.arange(ob, oe, dtype=np.int32), apm)
+        nb_full = (off2, tr2, mc2, np.arange(oe - ob + 1, dtype=np.int64) * 260,
+                   np.float32([0.004] * (oe - ob)))
+        ref = oracle.crs_semblance(full, nb_full, A, B, C, want_cube=True)
+        ok = (np.array_equal(np.diff(off), np.diff(off2)) and np.array_equal(mine.S, ref.S)
+              and np.array_equal(mine.best_idx, ref.best_idx) and np.array_equal(mine.stack, ref.stack))
+        t = sdist.max_over_ranks(float(rank) + 0.5)
+        q.put((rank, ok, t))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_crs_halo_exchange_matches_single_process(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ok, t in res:
+        assert ok, f"rank {rank} differs from the single-process result"
+        assert t == world - 0.5            # max over ranks of rank + 0.5
