@@ -89,6 +89,13 @@ const char* seis_last_error(void);
  * was skipped), else SEIS_OK. */
 int seis_device_status(void* stream);
 
+/* Self-test of the bounded device waits (no counterpart in the paper).  Launches one CTA
+ * that waits on a shared-memory mbarrier nothing completes, through the same bounded wait
+ * as the search kernels but with a limit of limit_us microseconds (1 .. 1e6); the wait
+ * gives up, records SEIS_ETIMEOUT in the device status word and the kernel returns, so the
+ * next seis_device_status() reports it and the context stays usable. */
+int seis_selftest_wait_timeout(int32_t limit_us, void* stream);
+
 /* Search kernel variants.  The semblance search kernels come in several tile shapes and
  * arithmetic forms (consumer warps per CTA, candidates per thread, scalar / packed f32x2 /
  * hybrid FP32 accumulation); every variant computes bit-identical results.  A launch uses

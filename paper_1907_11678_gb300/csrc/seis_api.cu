@@ -7,6 +7,7 @@
 #include <cstring>
 #include <vector>
 #include "seis.h"
+#include "seis_dev.cuh"
 #include "seis_internal.h"
 
 namespace seis {
@@ -321,5 +322,30 @@ extern "C" int seis_crs_aperture(const seis_gathers* d, const int32_t* central, 
     }
     e = cudaStreamSynchronize(s);   // host vectors above are released on return
     if (e != cudaSuccess) return cuda_fail(e, "seis_crs_aperture");
+    return SEIS_OK;
+}
+
+// ------------------------------------------------------------------ wait self-test ----
+namespace seis {
+
+// One thread waits on a shared-memory mbarrier whose phase never completes (its single
+// expected arrival never comes), through the same bounded wait the kernels use.
+__global__ void selftest_wait_kernel(unsigned long long limit_ns, unsigned* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!mbar_wait_bounded(&bar, 0u, limit_ns)) record_status(status, kStatusTimeout);
+    }
+}
+
+}  // namespace seis
+
+extern "C" int seis_selftest_wait_timeout(int32_t limit_us, void* stream) {
+    if (limit_us < 1 || limit_us > 1000000) return fail(SEIS_EINVAL, "limit_us outside [1, 1e6]");
+    selftest_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(
+        (unsigned long long)limit_us * 1000ull, device_status_word());
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "seis_selftest_wait_timeout");
     return SEIS_OK;
 }

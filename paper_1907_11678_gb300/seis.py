@@ -84,6 +84,7 @@ def load_library(path: str | None = None):
             lib.seis_batch_workspace_size.restype = ctypes.c_size_t
             lib.seis_batch_semblance.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, i32,
                                                  vp, vp, vp, vp, i64, vp, ctypes.c_size_t, vp]
+            lib.seis_selftest_wait_timeout.argtypes = [i32, vp]
             lib.seis_autotune_save.argtypes = [ctypes.c_char_p]
             lib.seis_autotune_load.argtypes = [ctypes.c_char_p]
             for name in ("seis_device_status", "cmp_semblance", "crs_semblance",
@@ -91,7 +92,8 @@ def load_library(path: str | None = None):
                          "seis_set_search_variant", "seis_get_search_variant",
                          "seis_autotune_cmp", "seis_autotune_crs", "seis_autotune_save",
                          "seis_autotune_load", "seis_autotune_clear", "stack",
-                         "crs_semblance_grad", "crs_refine", "seis_batch_semblance"):
+                         "crs_semblance_grad", "crs_refine", "seis_batch_semblance",
+                         "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -439,6 +441,11 @@ def batch_semblance(g: Gathers, b: Batch, w: int = 11, mode: int = 0, stream=Non
         b.out_rows, ctypes.c_void_p(aligned), b.workspace.numel() - (aligned - base),
         _stream_handle(stream)))
     return out
+
+
+def selftest_wait_timeout(limit_us: int = 10000, stream=None) -> None:
+    """Launch the bounded-wait self-test (include/seis.h: seis_selftest_wait_timeout)."""
+    _check(load_library().seis_selftest_wait_timeout(int(limit_us), _stream_handle(stream)))
 
 
 def device_status(stream=None) -> None:

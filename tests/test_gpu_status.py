@@ -1,0 +1,34 @@
+"""Failure detection without a GPU fault: a bounded device wait that nothing completes
+gives up, the status word reports SEIS_ETIMEOUT, and the context stays usable."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1907_11678_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def test_bounded_wait_gives_up_and_reports():
+    from paper_1907_11678_gb300 import build, seis
+    build.build()
+    seis.device_status()                              # clear anything earlier
+    t0 = time.perf_counter()
+    seis.selftest_wait_timeout(10000)                 # 10 ms limit on a wait nobody ends
+    with pytest.raises(seis.SeisError) as e:
+        seis.device_status()
+    elapsed = time.perf_counter() - t0
+    assert e.value.code == seis.SEIS_ETIMEOUT
+    assert elapsed < 5.0
+    seis.device_status()                              # cleared
+    # the context is still usable: a normal search runs and checks clean
+    ds = synth.cmp_line(2, 8, 200, 0.004, 0.0, 1000.0, 2, 2.0, seed=3)
+    g = seis.to_device(ds)
+    C = seis.velocity_grid(1400.0, 4500.0, 21)
+    out = seis.cmp_semblance(g, C, w=11)
+    torch.cuda.synchronize()
+    seis.device_status()
+    assert np.isfinite(out["best_S"].cpu().numpy()).all()
