@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
                 }
             }
             if (finished) {
-                if (lane == 0) sm.desc[slot] = StageDesc{0, 0, 0, 0, 1, 0, 0, 0};
+                if (lane == 0) sm.desc[slot] = make_desc(0, 0, 0u, 0, 0, 1);
                 __syncwarp();
                 mbar_arrive(&sm.full[slot]);
                 break;
@@ -146,15 +146,17 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
             }
             const int first = (pl_t == 0);
             int nfit = 0;
+            unsigned allv = 0u;
             const int ntr = produce_stage<true, HW>(
                 sm.buf[slot], sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h,
                 it.kind ? P.m : nullptr, nullptr, it.lbeg, it.M, pl_t, it.dt, it.mc, n0, n_last,
-                StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit);
+                StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit, allv);
             pl_t += nfit;
             const int last = (pl_t >= it.M);
             const int task_end = last && (pl_pass + 1 >= npass);
             if (lane == 0)
-                sm.desc[slot] = StageDesc{pl_pass, ntr, first, last, 0, (int)item, tile, task_end};
+                sm.desc[slot] = make_desc(pl_pass, ntr, allv, first, last, 0, (int)item, tile,
+                                          task_end);
             if (last) { ++pl_pass; pl_t = 0; }
             __syncwarp();
             mbar_arrive(&sm.full[slot]);
@@ -189,8 +191,8 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
         const StageDesc d = sm.desc[slot];
         if (d.end) break;
         if (d.first && d.pass == 0) {            // a new task
-            it = load_item(P, d.pad0);
-            nrow = d.pad1 * 32 + lane;
+            it = load_item(P, d.item);
+            nrow = d.tile * 32 + lane;
             act = nrow < it.nrows;
             rc = row_const(act, nrow);
         }
@@ -198,9 +200,9 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
         const int ntr = min(d.ntr, kChunkT);
         const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
         if (ntr > 0 && acc.cidx[0] < it.ncand)
-            accum_stage<true, W, CFG>(acc, sm.meta[slot], ntr, slot_base, rc, zidx, smf);
+            accum_stage<true, W, CFG>(acc, sm.meta[slot], ntr, d.allv, slot_base, rc, zidx, smf);
         if (d.last) accum_end(acc, it.ncand, nullptr, bestS, bestC, bestT);
-        if (d.pad2) {                            // the task's last stage: argmax and outputs
+        if (d.task_end) {                        // the task's last stage: argmax and outputs
             sm.redS[warp][lane] = bestS;
             sm.redC[warp][lane] = bestC;
             sm.redT[warp][lane] = bestT;

@@ -89,19 +89,20 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
             }
             __syncwarp();
             if (sm.abort_flag || done) {
-                if (lane == 0) sm.desc[slot] = StageDesc{0, 0, 0, 0, 1, 0, 0, 0};
+                if (lane == 0) sm.desc[slot] = make_desc(0, 0, 0u, 0, 0, 1);
                 __syncwarp();
                 mbar_arrive(&sm.full[slot]);
                 break;
             }
             int nfit = 0;
+            unsigned allv = 0u;                 // unused: this kernel checks every pair
             const int ntr = produce_stage<CRS, HW>(sm.buf[slot], sm.meta[slot], &sm.full[slot],
                                                    P.traces, P.trace_off, P.h, P.m, P.list, lbeg,
                                                    M, pl_t, dt, mc, n0, n_last, bnd, P.status,
-                                                   nfit);
+                                                   nfit, allv);
             pl_t += nfit;
             done = pl_t >= M;
-            if (lane == 0) sm.desc[slot] = StageDesc{0, ntr, 0, 0, 0, 0, 0, 0};
+            if (lane == 0) sm.desc[slot] = make_desc(0, ntr, 0u, 0, 0, 0);
             __syncwarp();
             mbar_arrive(&sm.full[slot]);
         }

@@ -81,8 +81,21 @@ struct __align__(16) TraceMeta {
 };
 
 struct __align__(16) StageDesc {
-    int pass, ntr, first, last, end, pad0, pad1, pad2;
+    int pass;          // candidate pass
+    int ntr;           // traces staged (compacted, in list order)
+    unsigned allv;     // bit t: every (row, candidate) of the stage takes part for trace t
+    int first, last;   // first / last stage of the pass
+    int end;           // no more stages
+    int item, tile;    // batch kernel: the task
+    int task_end;      // batch kernel: last stage of the task
+    int pad0, pad1, pad2;
 };
+
+__device__ __forceinline__ StageDesc make_desc(int pass, int ntr, unsigned allv, int first,
+                                               int last, int end, int item = 0, int tile = 0,
+                                               int task_end = 0) {
+    return StageDesc{pass, ntr, allv, first, last, end, item, tile, task_end, 0, 0, 0};
+}
 
 struct SearchSmem {
     float buf[kSlots][kBuf];
@@ -288,13 +301,15 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
                                              const float* hh, const float* mm, const int32_t* list,
                                              int64_t lbeg, int M, int pl_t, float dt, float mc,
                                              int n0, int n_last, const StageBounds& b,
-                                             unsigned* status, int& nfit_out) {
+                                             unsigned* status, int& nfit_out,
+                                             unsigned& allv_out) {
     const int lane = threadIdx.x & 31;
     const float bA0 = b.A0, bA1 = b.A1, bB0 = b.B0, bB1 = b.B1, bC0 = b.C0, bC1 = b.C1;
     fence_proxy_async_smem();   // earlier generic accesses of the slot before async writes
     const int t = pl_t + lane;
     const bool v = t < M;
     int len = 0, n_el = 0, mis = 0, lo = 0;
+    bool allv = false;
     const float* src = nullptr;
     TraceMeta tm{0, 1, 0, 0.f, 0.f, 0.f, 0, 0};
     if (v) {
@@ -325,8 +340,13 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
         if (pHi >= 0.f && radHi >= 0.f) {
             const float uLo = fminf(sqrtf(fmaxf(radLo, 0.f)), 1.6e7f);
             const float uHi = fminf(sqrtf(radHi), 1.6e7f);
-            const int kmin = max((int)floorf(uLo) - 2, HW);
-            const int kmax = min((int)floorf(uHi) + 2, ns_i - HW - 2);
+            const int klo = (int)floorf(uLo) - 2, khi = (int)floorf(uHi) + 2;
+            const int kmin = max(klo, HW);
+            const int kmax = min(khi, ns_i - HW - 2);
+            // every pair of the box takes part: the traveltime is real with margin, and
+            // the whole k range (with the +-2 margin) lies inside the trace's mask
+            allv = klo >= HW && khi <= ns_i - HW - 2 && (!CRS || (float)n0 + aLo >= 1e-3f) &&
+                   radLo >= 1.f;
             if (kmin <= kmax) {
                 tm.kmin = kmin;
                 tm.kmax = kmax;
@@ -348,16 +368,19 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
     // traces whose window is empty for this stage are left out of it
     const unsigned present = __ballot_sync(kFull, lane < nfit && n_el > 0);
     int ntr = __popc(present);
+    const int pos = __popc(present & ((1u << lane) - 1u));
+    allv_out = __reduce_or_sync(kFull, ((present >> lane) & 1u) && allv ? (1u << pos) : 0u);
     if (nfit == 0 && M > pl_t) {
         // a single window larger than a slot (traces are limited on the host so this
         // cannot happen): drop that trace and record it
         if (lane == 0) record_status(status, kStatusOverflow);
         nfit = 1;
         ntr = 0;
+        allv_out = 0u;
     } else if (lane < nfit && n_el > 0) {
         const int off = pre - len;                       // multiple of 4 floats
         tm.base = off + mis - lo;
-        meta[__popc(present & ((1u << lane) - 1u))] = tm;
+        meta[pos] = tm;
         float* dst = slotbuf + off + mis;
         const int head = min((4 - mis) & 3, n_el);
         const int nb = (n_el - head) & ~3;
@@ -370,6 +393,66 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
     }
     nfit_out = nfit;
     return ntr;
+}
+
+// Check-free forms for traces on which every pair of the stage takes part: no mask test,
+// no select.  kk is clamped into the staged window only to keep every read inside it
+// (rows past the owner's end and candidates past ncand land there; their sums are
+// discarded).
+template <bool CRS>
+__device__ __forceinline__ void intersect_one_fast(float A, float B, float C, const TraceConst& tc,
+                                                   float nf, float nsq, int& idx, float& x) {
+    float D;
+    if (CRS) {
+        const float a = A * tc.e;
+        const float pp = nf + a;
+        const float rr = fmaf(B, tc.g, C * tc.q);
+        D = fmaf(rr, rcp_fast(fmaxf(sqrt_fast(fmaf(pp, pp, rr)) + pp, 1e-30f)), a);
+    } else {
+        const float cq = C * tc.q;
+        D = cq * rcp_fast(sqrt_fast(nsq + cq) + nf);
+    }
+    const float t = __fadd_rd(D, kFloorShift);
+    const unsigned kk = min((unsigned)(__float_as_int(t) + tc.off), tc.rng);
+    x = D - (t - kFloorShift);
+    idx = tc.kbase + (int)kk;
+}
+
+template <bool CRS>
+__device__ __forceinline__ void intersect_pair_fast(f2_t A2, f2_t B2, f2_t C2, const TraceConst& tc,
+                                                    f2_t nf2, f2_t nsq2, int& ia, int& ib,
+                                                    float& xa, float& xb) {
+    const f2_t q2 = pk2(tc.q, tc.q);
+    f2_t D2;
+    if (CRS) {
+        const f2_t a2 = mul2(A2, pk2(tc.e, tc.e));
+        const f2_t pp2 = add2(nf2, a2);
+        const f2_t rr2 = fma2(B2, pk2(tc.g, tc.g), mul2(C2, q2));
+        const f2_t rad2 = fma2(pp2, pp2, rr2);
+        float ra, rb;
+        up2(rad2, ra, rb);
+        const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), pp2);
+        float sa, sb;
+        up2(sum2, sa, sb);
+        D2 = fma2(rr2, pk2(rcp_fast(fmaxf(sa, 1e-30f)), rcp_fast(fmaxf(sb, 1e-30f))), a2);
+    } else {
+        const f2_t cq2 = mul2(C2, q2);
+        const f2_t rad2 = add2(nsq2, cq2);
+        float ra, rb;
+        up2(rad2, ra, rb);
+        const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), nf2);
+        float sa, sb;
+        up2(sum2, sa, sb);
+        D2 = mul2(cq2, pk2(rcp_fast(sa), rcp_fast(sb)));
+    }
+    const f2_t shift2 = pk2(kFloorShift, kFloorShift);
+    const f2_t t2 = add2_rm(D2, shift2);
+    const f2_t x2 = sub2(D2, sub2(t2, shift2));
+    float ta, tb;
+    up2(t2, ta, tb);
+    up2(x2, xa, xb);
+    ia = tc.kbase + (int)min((unsigned)(__float_as_int(ta) + tc.off), tc.rng);
+    ib = tc.kbase + (int)min((unsigned)(__float_as_int(tb) + tc.off), tc.rng);
 }
 
 // ---- consumer-side accumulation, shared by the search kernel and the batch kernel -----
@@ -436,12 +519,13 @@ __device__ __forceinline__ void accum_begin(Accum<W, CFG>& a, int c0, int ncand,
     }
 }
 
-// Accumulate the ntr staged traces of one slot.  Software pipeline: the traveltimes of
-// trace t+1 (long MUFU chains) are formed while the window of trace t is accumulated.
-template <bool CRS, int W, class CFG>
-__device__ __forceinline__ void accum_stage(Accum<W, CFG>& a, const TraceMeta* meta, int ntr,
-                                            int slot_base, const RowConst& rc, int zidx,
-                                            const float* smf) {
+// Accumulate one run of traces [t0, t1) of a slot whose traces are all of one kind (FAST:
+// every pair takes part).  Software pipeline: the traveltimes of trace t+1 (long MUFU
+// chains) are formed while the window of trace t is accumulated.
+template <bool CRS, int W, class CFG, bool FAST>
+__device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* meta, int t0, int t1,
+                                          int slot_base, const RowConst& rc, int zidx,
+                                          const float* smf) {
     constexpr int HW = W / 2;
     constexpr int kR = CFG::kR;
     constexpr int kG = Accum<W, CFG>::kG;
@@ -452,28 +536,38 @@ __device__ __forceinline__ void accum_stage(Accum<W, CFG>& a, const TraceMeta* m
         const TraceConst tc = trace_const(meta[t], rc.n, slot_base, HW);
         if constexpr (CFG::kMode == kPacked) {
             #pragma unroll
-            for (int g = 0; g < kG; ++g)
-                intersect_pair<CRS>(a.A2[g], a.B2[g], a.C2[g], tc, rc.nf2, rc.nsq2, zidx, sI[2 * g],
-                                    sI[2 * g + 1], sX[2 * g], sX[2 * g + 1], sO[2 * g],
-                                    sO[2 * g + 1]);
+            for (int g = 0; g < kG; ++g) {
+                if constexpr (FAST)
+                    intersect_pair_fast<CRS>(a.A2[g], a.B2[g], a.C2[g], tc, rc.nf2, rc.nsq2,
+                                             sI[2 * g], sI[2 * g + 1], sX[2 * g], sX[2 * g + 1]);
+                else
+                    intersect_pair<CRS>(a.A2[g], a.B2[g], a.C2[g], tc, rc.nf2, rc.nsq2, zidx,
+                                        sI[2 * g], sI[2 * g + 1], sX[2 * g], sX[2 * g + 1],
+                                        sO[2 * g], sO[2 * g + 1]);
+            }
         } else {
             #pragma unroll
-            for (int r = 0; r < kR; ++r)
-                intersect_one<CRS>(a.Ar[r], a.Br[r], a.Cr[r], tc, rc.nf, rc.nsq, zidx, sI[r],
-                                   sX[r], sO[r]);
+            for (int r = 0; r < kR; ++r) {
+                if constexpr (FAST)
+                    intersect_one_fast<CRS>(a.Ar[r], a.Br[r], a.Cr[r], tc, rc.nf, rc.nsq, sI[r],
+                                            sX[r]);
+                else
+                    intersect_one<CRS>(a.Ar[r], a.Br[r], a.Cr[r], tc, rc.nf, rc.nsq, zidx, sI[r],
+                                       sX[r], sO[r]);
+            }
         }
     };
-    setup(0);
-    for (int t = 0; t < ntr; ++t) {
+    setup(t0);
+    for (int t = t0; t < t1; ++t) {
         int cI[kR];
         float cX[kR];
         #pragma unroll
         for (int r = 0; r < kR; ++r) {
             cI[r] = sI[r];
             cX[r] = sX[r];
-            a.cntv[r] += sO[r] ? 1 : 0;
+            if constexpr (!FAST) a.cntv[r] += sO[r] ? 1 : 0;
         }
-        setup(min(t + 1, ntr - 1));
+        setup(min(t + 1, t1 - 1));
         #pragma unroll
         for (int g = 0; g < kG; ++g) {
             if constexpr (CFG::kMode == kScalar) {
@@ -509,6 +603,29 @@ __device__ __forceinline__ void accum_stage(Accum<W, CFG>& a, const TraceMeta* m
                 }
             }
         }
+    }
+    if constexpr (FAST) {
+        #pragma unroll
+        for (int r = 0; r < kR; ++r) a.cntv[r] += t1 - t0;
+    }
+}
+
+// Accumulate the ntr staged traces of one slot, in list order, as runs of all-valid traces
+// (bit t of allv) and checked traces.  The order of the sums is the list order whatever
+// the runs, so every tile shape gives bit-identical results.
+template <bool CRS, int W, class CFG>
+__device__ __forceinline__ void accum_stage(Accum<W, CFG>& a, const TraceMeta* meta, int ntr,
+                                            unsigned allv, int slot_base, const RowConst& rc,
+                                            int zidx, const float* smf) {
+    int t = 0;
+    while (t < ntr) {
+        const bool fast = (allv >> t) & 1u;
+        const unsigned rest = (fast ? ~allv : allv) >> t;    // first trace of the other kind
+        const int len = rest ? __ffs(rest) - 1 : 32;
+        const int t1 = min(ntr, t + len);
+        if (fast) accum_run<CRS, W, CFG, true>(a, meta, t, t1, slot_base, rc, zidx, smf);
+        else accum_run<CRS, W, CFG, false>(a, meta, t, t1, slot_base, rc, zidx, smf);
+        t = t1;
     }
 }
 
@@ -623,7 +740,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
             }
             __syncwarp();
             if (sm.abort_flag || pl_pass >= npass) {
-                if (lane == 0) sm.desc[slot] = StageDesc{0, 0, 0, 0, 1, 0, 0, 0};
+                if (lane == 0) sm.desc[slot] = make_desc(0, 0, 0u, 0, 0, 1);
                 __syncwarp();
                 mbar_arrive(&sm.full[slot]);
                 break;
@@ -640,13 +757,14 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
             }
             const int first = (pl_t == 0);
             int nfit = 0;
+            unsigned allv = 0u;
             const int ntr = produce_stage<CRS, HW>(
                 sm.buf[slot], sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h, P.m,
                 P.list, lbeg, M, pl_t, dt, mc, n0, n_last,
-                StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit);
+                StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit, allv);
             pl_t += nfit;
             const int last = (pl_t >= M);
-            if (lane == 0) sm.desc[slot] = StageDesc{pl_pass, ntr, first, last, 0, 0, 0, 0};
+            if (lane == 0) sm.desc[slot] = make_desc(pl_pass, ntr, allv, first, last, 0);
             if (last) { ++pl_pass; pl_t = 0; }
             __syncwarp();
             mbar_arrive(&sm.full[slot]);
@@ -690,7 +808,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
         const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
         // a warp whose candidates of this pass all lie past the end skips the stage
         if (ntr > 0 && acc.cidx[0] < P.ncand)
-            accum_stage<CRS, W, CFG>(acc, sm.meta[slot], ntr, slot_base, rc, zidx, smf);
+            accum_stage<CRS, W, CFG>(acc, sm.meta[slot], ntr, d.allv, slot_base, rc, zidx, smf);
         if (d.last)
             accum_end(acc, P.ncand, (P.S_cube && act) ? P.S_cube + (row0 + n) * (int64_t)P.ncand
                                                       : nullptr, bestS, bestC, bestT);
