@@ -194,9 +194,11 @@ int crs_semblance_grad(const seis_gathers* d, const seis_aperture* ap, const flo
 
 /* Gradient-ascent refinement of the CRS operators (no counterpart in the paper; it replaces
  * the dense 3-D grid search of Section 2.2 by a local search from a coarse pick).  Per row,
- * in normalised coordinates z = (theta - lo3) / (hi3 - lo3): starting from ABC_inout, `steps`
- * trials z' = clamp(z + s g/|g|, 0, 1) with g = dS/dz; a trial is accepted when its S is
- * not lower, otherwise s halves (s starts at step0).  On return ABC_inout holds the accepted
+ * in normalised coordinates z = (theta - lo3) / (hi3 - lo3), with g = dS/dz: starting from
+ * ABC_inout, `steps` projected quasi-Newton trials z' = clamp(z + a d, 0, 1), d = H g, where H
+ * (the inverse-curvature estimate, BFGS-updated after each accepted trial) starts as
+ * (step0/|g|) I and |d| is capped at 0.25; a trial is accepted when its S is not lower, and a
+ * rejected trial halves a (a = 1 after each acceptance).  On return ABC_inout holds the accepted
  * operators and S_out, grad_out [rows][3], stack_out their semblance, gradient and stack.
  * lo3, hi3: HOST arrays of 3 floats.  rows = ap->out_off[n_central] (host).  workspace:
  * device scratch of seis_refine_workspace_size(rows) bytes, 256-byte aligned, owned by the
@@ -206,6 +208,30 @@ int crs_refine(const seis_gathers* d, const seis_aperture* ap, float* ABC_inout,
                const float* lo3, const float* hi3, int32_t steps, float step0, int32_t w,
                float* S_out, float* grad_out, float* stack_out,
                void* workspace, size_t ws_bytes, int64_t rows, void* stream);
+
+/* Starting points for a multi-start refinement (no counterpart in the paper): from a coarse
+ * CRS semblance cube S_cube [rows][nA*nB*nC] (device, as crs_semblance writes it, candidate
+ * cand = (ia*nB + ib)*nC + ic), the nstart best candidates of every row in the order
+ * S descending, candidate index ascending on ties, decoded to ABC_starts [nstart][rows][3]
+ * (device, caller-owned; start j of row r at (j*rows + r)*3).  A, B, C: device axes.
+ * 1 <= nstart <= nA*nB*nC.  Asynchronous, one launch.  Errors: SEIS_EINVAL, SEIS_ECUDA. */
+int crs_top_starts(const float* S_cube, int64_t rows, const float* A, int32_t nA,
+                   const float* B, int32_t nB, const float* C, int32_t nC, int32_t nstart,
+                   float* ABC_starts, void* stream);
+
+/* Multi-start refinement (no counterpart in the paper): crs_refine from each of the nstart
+ * starting operators ABC_starts [nstart][rows][3] (device, read only), keeping per row the
+ * result with the highest S (the earlier start on ties) in ABC_out [rows][3], S_out,
+ * grad_out [rows][3] and stack_out [rows].  Other arguments as crs_refine; workspace:
+ * seis_refine_multi_workspace_size(rows) bytes, 256-byte aligned, caller-owned.
+ * Asynchronous (nstart * (3 + 2*steps) operations on stream).  Errors: SEIS_EINVAL,
+ * SEIS_ECUDA. */
+size_t seis_refine_multi_workspace_size(int64_t rows);
+int crs_refine_multi(const seis_gathers* d, const seis_aperture* ap, const float* ABC_starts,
+                     int32_t nstart, const float* lo3, const float* hi3, int32_t steps,
+                     float step0, int32_t w, float* ABC_out, float* S_out, float* grad_out,
+                     float* stack_out, void* workspace, size_t ws_bytes, int64_t rows,
+                     void* stream);
 
 /* Batched search (no counterpart in the paper: its CGs take one CDP per task, Section 3.5;
  * here thousands of uneven CMP gathers and CRS supergathers run in ONE persistent launch

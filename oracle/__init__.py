@@ -12,8 +12,10 @@ event and an exactly-sampled dipping plane (S = 1 at the true operator), a
 hand-derived worked example under tests/golden/, a pure-Python brute force on tiny
 inputs, numpy.interp for the stack of a single trace, the CRS -> CMP reductions and
 central finite differences of the gradient.  The refinement (reading c16) is pinned
-only by its invariants (monotone S, bounds respected), so its result is
-"parity unpinned" beyond them.
+only by its invariants (monotone S, bounds respected, the exact operator of a sampled
+plane reached from a nearby start, the best of several starts never below any one of
+them), so its result is "parity unpinned" beyond them.  The start selection
+(top_starts) is pinned by hand-worked rows with ties.
 """
 from __future__ import annotations
 
@@ -235,6 +237,39 @@ def crs_refine(ds, nb, theta0, lo3, hi3, steps=20, step0=0.05, w=11, rows=None,
     if rc != 0:
         raise ValueError("seis_oracle_crs_refine: invalid arguments")
     return Result(theta=th, S=S, grad=grad, stack=st)
+
+
+def top_starts(S_cube, A, B, C, nstart):
+    """The nstart best candidates of every row of a CRS cube [rows, nA*nB*nC], ordered by
+    S descending and candidate index ascending on ties, as operators [nstart, rows, 3]
+    with cand = (ia*nB + ib)*nC + ic (the starts of a multi-start refinement, reading c16).
+    Plain definition: a stable sort of each row."""
+    S_cube = np.asarray(S_cube)
+    A, B, C = (np.asarray(v) for v in (A, B, C))
+    nB, nC = len(B), len(C)
+    out = np.empty((nstart, S_cube.shape[0], 3), np.float64)
+    for r in range(S_cube.shape[0]):
+        order = sorted(range(S_cube.shape[1]), key=lambda c: (-S_cube[r, c], c))[:nstart]
+        for j, c in enumerate(order):
+            out[j, r] = (A[c // (nB * nC)], B[(c // nC) % nB], C[c % nC])
+    return out
+
+
+def crs_refine_multi(ds, nb, starts, lo3, hi3, steps=20, step0=0.05, w=11, rows=None,
+                     nthreads=0) -> Result:
+    """crs_refine from each start [nstart, rows, 3]; per row the result with the highest
+    S is kept, the earlier start on ties (reading c16)."""
+    best = None
+    for k in range(len(starts)):
+        r = crs_refine(ds, nb, starts[k], lo3, hi3, steps=steps, step0=step0, w=w, rows=rows,
+                       nthreads=nthreads)
+        if best is None:
+            best = r
+            continue
+        better = r.S > best.S
+        for key in ("theta", "S", "grad", "stack"):
+            best[key][better] = r[key][better]
+    return best
 
 
 def cmp_as_crs(ds, gathers=None):

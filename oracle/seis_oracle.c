@@ -445,11 +445,53 @@ int seis_oracle_crs_eval(const float* traces, const int64_t* trace_off, const fl
 }
 
 /* ------------------------------------------------------------------------- */
+/* 3-vector and 3x3 helpers of the refinement. */
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static double norm3(const double* a) { return sqrt(dot3(a, a)); }
+static void mat3_vec(double H[3][3], const double* v, double* out)
+{
+    for (int i = 0; i < 3; ++i) out[i] = H[i][0] * v[0] + H[i][1] * v[1] + H[i][2] * v[2];
+}
+/* H = (step0/|g|) I: the first step along g has length step0. */
+static void reset_inverse_curvature(double H[3][3], const double* g, double step0)
+{
+    const double gn = norm3(g);
+    const double h0 = gn > 0.0 ? step0 / gn : 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) H[i][j] = (i == j) ? h0 : 0.0;
+}
+/* BFGS update of the inverse curvature estimate with step s and gradient change y (s.y > 0):
+ * H <- (I - rho s y') H (I - rho y s') + rho s s', rho = 1/(s.y), written as matrix products. */
+static void bfgs_inverse_update(double H[3][3], const double* s, const double* y, double sy)
+{
+    const double rho = 1.0 / sy;
+    double L[3][3], T[3][3], N[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) L[i][j] = (i == j ? 1.0 : 0.0) - rho * s[i] * y[j];
+    for (int i = 0; i < 3; ++i)                        /* T = L H */
+        for (int j = 0; j < 3; ++j)
+            T[i][j] = L[i][0] * H[0][j] + L[i][1] * H[1][j] + L[i][2] * H[2][j];
+    for (int i = 0; i < 3; ++i)                        /* N = T L' + rho s s' */
+        for (int j = 0; j < 3; ++j)
+            N[i][j] = T[i][0] * L[j][0] + T[i][1] * L[j][1] + T[i][2] * L[j][2] +
+                      rho * s[i] * s[j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) H[i][j] = N[i][j];
+}
+
 /* Gradient-ascent refinement of the CRS operator from a coarse pick (reading c16).
- * Per row, in normalised coordinates z = (theta - lo) / (hi - lo):
- *   start at z0 (theta_in), step s = step0; evaluate S(z), g = dS/dz;
- *   repeat `steps` times: if |g| == 0 stop; trial z' = clamp(z + s g/|g|, 0, 1);
- *     evaluate S(z'); if S(z') >= S(z) accept (z, S, g) <- (z', S', g'), else s <- s/2.
+ * Per row, in normalised coordinates z = (theta - lo) / (hi - lo), g = dS/dz, a projected
+ * quasi-Newton (BFGS) ascent with step halving:
+ *   evaluate S(z0), g(z0); H = (step0/|g|) I (the inverse curvature estimate); a = 1;
+ *   repeat `steps` times:
+ *     if |g| == 0 stop;
+ *     d = H g; if d.g <= 0 reset H = (step0/|g|) I and d = H g;
+ *     if |d| > 0.25 shrink d to length 0.25;
+ *     trial z' = clamp(z + a d, 0, 1); evaluate S(z'), g(z');
+ *     if S(z') >= S(z): with s = z' - z, y = g - g' (the gradient change of -S), and
+ *       s.y > 1e-6 |s||y|, update H <- (I - s y'/s.y) H (I - y s'/s.y) + s s'/s.y;
+ *       accept (z, S, g) <- (z', S', g'); a = 1;
+ *     else a <- a/2.
  * Outputs theta_out [nrows*3], S_out, grad_out (dS/dtheta at the final point, may be
  * NULL), stack_out (may be NULL). */
 int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const float* h,
@@ -482,25 +524,42 @@ int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const 
         }
         crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th, &s, g, &st, NULL,
                      NULL, 0.0);
-        double step = step0;
+        double span[3], H[3][3], al = 1.0;
+        for (int a = 0; a < 3; ++a) span[a] = hi3[a] - lo3[a];
+        for (int a = 0; a < 3; ++a) gz[a] = g[a] * span[a];
+        reset_inverse_curvature(H, gz, step0);
         for (int it = 0; it < steps; ++it) {
-            double gn = 0.0;
-            for (int a = 0; a < 3; ++a) { gz[a] = g[a] * (hi3[a] - lo3[a]); gn += gz[a] * gz[a]; }
-            gn = sqrt(gn);
-            if (!(gn > 0.0)) break;
+            for (int a = 0; a < 3; ++a) gz[a] = g[a] * span[a];
+            if (!(norm3(gz) > 0.0)) break;
+            double d[3];
+            mat3_vec(H, gz, d);
+            if (!(dot3(d, gz) > 0.0)) {
+                reset_inverse_curvature(H, gz, step0);
+                mat3_vec(H, gz, d);
+            }
+            const double dn = norm3(d);
+            if (dn > 0.25) for (int a = 0; a < 3; ++a) d[a] *= 0.25 / dn;
             double z2[3], th2[3], g2[3], s2, st2;
             for (int a = 0; a < 3; ++a) {
-                double zz = z[a] + step * gz[a] / gn;
+                double zz = z[a] + al * d[a];
                 z2[a] = zz < 0.0 ? 0.0 : (zz > 1.0 ? 1.0 : zz);
-                th2[a] = lo3[a] + z2[a] * (hi3[a] - lo3[a]);
+                th2[a] = lo3[a] + z2[a] * span[a];
             }
             crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th2, &s2, g2, &st2,
                          NULL, NULL, 0.0);
             if (s2 >= s) {
+                double sv[3], yv[3];
+                for (int a = 0; a < 3; ++a) {
+                    sv[a] = z2[a] - z[a];
+                    yv[a] = g[a] * span[a] - g2[a] * span[a];
+                }
+                const double sy = dot3(sv, yv);
+                if (sy > 1e-6 * norm3(sv) * norm3(yv)) bfgs_inverse_update(H, sv, yv, sy);
                 for (int a = 0; a < 3; ++a) { z[a] = z2[a]; th[a] = th2[a]; g[a] = g2[a]; }
                 s = s2; st = st2;
+                al = 1.0;
             } else {
-                step *= 0.5;
+                al *= 0.5;
             }
         }
         for (int a = 0; a < 3; ++a) theta_out[3 * e + a] = th[a];

@@ -97,28 +97,17 @@ extern "C" size_t seis_refine_workspace_size(int64_t rows) {
     if (rows < 0) return 0;
     const size_t r = (size_t)rows;
     return align256(r * 3 * 4) + align256(r * 4) + align256(r * 3 * 4) + align256(r * 4) +
-           align256(r * 4);
+           align256(r * 4) + align256(r * 6 * 4);
 }
 
-extern "C" int crs_refine(const seis_gathers* d, const seis_aperture* ap, float* ABC_inout,
-                          const float* lo3, const float* hi3, int32_t steps, float step0,
-                          int32_t w, float* S_out, float* grad_out, float* stack_out,
-                          void* workspace, size_t ws_bytes, int64_t rows, void* stream) {
-    if (!ap) return fail(SEIS_EINVAL, "aperture descriptor is NULL");
-    EvalParams p;
-    int64_t dummy;
-    int rc = build_eval(d, ap, ABC_inout, w, &p, &dummy);
-    if (rc) return rc;
-    if (!lo3 || !hi3) return fail(SEIS_EINVAL, "lo3 / hi3 are NULL");
-    for (int a = 0; a < 3; ++a)
-        if (!(hi3[a] > lo3[a])) return fail(SEIS_EINVAL, "hi3[%d] must exceed lo3[%d]", a, a);
-    if (steps < 0 || !(step0 > 0.f)) return fail(SEIS_EINVAL, "steps >= 0 and step0 > 0 needed");
-    if (!S_out || !grad_out || !stack_out) return fail(SEIS_EINVAL, "an output array is NULL");
-    if (rows < 1) return fail(SEIS_EINVAL, "rows must be >= 1");
-    if (!workspace || ws_bytes < seis_refine_workspace_size(rows))
-        return fail(SEIS_EINVAL, "workspace of %zu bytes needed", seis_refine_workspace_size(rows));
-    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
-        return fail(SEIS_EINVAL, "workspace must be 256-byte aligned");
+namespace seis {
+
+// The refinement loop of crs_refine on caller-checked arguments: theta [rows][3] in/out,
+// S, grad, stack outputs, ws of seis_refine_workspace_size(rows) bytes (256-aligned).
+int refine_run(const EvalParams& p0, float* theta, const float* lo3, const float* hi3,
+               int32_t steps, float step0, int32_t w, float* S_out, float* grad_out,
+               float* stack_out, void* workspace, int64_t rows, cudaStream_t s) {
+    EvalParams p = p0;
     char* ws = static_cast<char*>(workspace);
     const size_t r = (size_t)rows;
     float* trial_theta = reinterpret_cast<float*>(ws);
@@ -130,11 +119,12 @@ extern "C" int crs_refine(const seis_gathers* d, const seis_aperture* ap, float*
     float* trial_stack = reinterpret_cast<float*>(ws);
     ws += align256(r * 4);
     float* step = reinterpret_cast<float*>(ws);
+    ws += align256(r * 4);
+    float* Hinv = reinterpret_cast<float*>(ws);
 
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     RefineParams u{};
     u.rows = rows;
-    u.theta = ABC_inout;
+    u.theta = theta;
     u.S = S_out;
     u.grad = grad_out;
     u.stack = stack_out;
@@ -143,11 +133,12 @@ extern "C" int crs_refine(const seis_gathers* d, const seis_aperture* ap, float*
     u.trial_grad = trial_grad;
     u.trial_stack = trial_stack;
     u.step = step;
+    u.H = Hinv;
     for (int a = 0; a < 3; ++a) { u.lo[a] = lo3[a]; u.hi[a] = hi3[a]; }
     u.step0 = step0;
 
     // evaluate the starting operators
-    p.theta = ABC_inout;
+    p.theta = theta;
     p.S = trial_S;
     p.grad = trial_grad;
     p.stack = trial_stack;
@@ -166,4 +157,42 @@ extern "C" int crs_refine(const seis_gathers* d, const seis_aperture* ap, float*
         if ((e = launch_refine_update(u, s)) != cudaSuccess) return cuda_fail(e, "crs_refine update");
     }
     return SEIS_OK;
+}
+
+// Argument checks shared by crs_refine and crs_refine_multi.
+int refine_check(const seis_gathers* d, const seis_aperture* ap, const float* theta,
+                 const float* lo3, const float* hi3, int32_t steps, float step0, int32_t w,
+                 const float* S_out, const float* grad_out, const float* stack_out,
+                 const void* workspace, size_t ws_bytes, size_t ws_needed, int64_t rows,
+                 EvalParams* p) {
+    if (!ap) return fail(SEIS_EINVAL, "aperture descriptor is NULL");
+    int64_t dummy;
+    int rc = build_eval(d, ap, theta, w, p, &dummy);
+    if (rc) return rc;
+    if (!lo3 || !hi3) return fail(SEIS_EINVAL, "lo3 / hi3 are NULL");
+    for (int a = 0; a < 3; ++a)
+        if (!(hi3[a] > lo3[a])) return fail(SEIS_EINVAL, "hi3[%d] must exceed lo3[%d]", a, a);
+    if (steps < 0 || !(step0 > 0.f)) return fail(SEIS_EINVAL, "steps >= 0 and step0 > 0 needed");
+    if (!S_out || !grad_out || !stack_out) return fail(SEIS_EINVAL, "an output array is NULL");
+    if (rows < 1) return fail(SEIS_EINVAL, "rows must be >= 1");
+    if (!workspace || ws_bytes < ws_needed)
+        return fail(SEIS_EINVAL, "workspace of %zu bytes needed", ws_needed);
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+        return fail(SEIS_EINVAL, "workspace must be 256-byte aligned");
+    return SEIS_OK;
+}
+
+}  // namespace seis
+
+extern "C" int crs_refine(const seis_gathers* d, const seis_aperture* ap, float* ABC_inout,
+                          const float* lo3, const float* hi3, int32_t steps, float step0,
+                          int32_t w, float* S_out, float* grad_out, float* stack_out,
+                          void* workspace, size_t ws_bytes, int64_t rows, void* stream) {
+    EvalParams p;
+    int rc = refine_check(d, ap, ABC_inout, lo3, hi3, steps, step0, w, S_out, grad_out,
+                          stack_out, workspace, ws_bytes, seis_refine_workspace_size(rows), rows,
+                          &p);
+    if (rc) return rc;
+    return refine_run(p, ABC_inout, lo3, hi3, steps, step0, w, S_out, grad_out, stack_out,
+                      workspace, rows, static_cast<cudaStream_t>(stream));
 }

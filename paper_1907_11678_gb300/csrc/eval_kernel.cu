@@ -230,42 +230,102 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
     }
 }
 
+// Inverse curvature estimate of one row, symmetric 3x3 stored as H00 H01 H02 H11 H12 H22.
+__device__ __forceinline__ void h_reset(float* H, const float* gz, float step0) {
+    const float gn = sqrtf(gz[0] * gz[0] + gz[1] * gz[1] + gz[2] * gz[2]);
+    const float h0 = gn > 0.f ? step0 / gn : 0.f;
+    H[0] = h0; H[1] = 0.f; H[2] = 0.f; H[3] = h0; H[4] = 0.f; H[5] = h0;
+}
+
+__device__ __forceinline__ void h_mul(const float* H, const float* v, float* o) {
+    o[0] = H[0] * v[0] + H[1] * v[1] + H[2] * v[2];
+    o[1] = H[1] * v[0] + H[3] * v[1] + H[4] * v[2];
+    o[2] = H[2] * v[0] + H[4] * v[1] + H[5] * v[2];
+}
+
+// One refinement step per row: judge the evaluated trial, then propose the next one.  The
+// rule is a projected quasi-Newton (BFGS) ascent of S in normalised coordinates
+// z = (theta - lo) / (hi - lo) with step halving on a failed trial:
+//   d = H g (H reset to (step0/|g|) I when d is not an ascent direction), |d| <= 0.25,
+//   trial z + a d clamped to [0, 1]; an accepted trial updates H with the expanded BFGS
+//   inverse update  H += -rho (u s' + s u') + (rho + rho^2 y.u) s s',  u = H y,
+//   rho = 1/(s.y), s = step, y = g - g' (gradient change of -S), when s.y > 1e-6 |s||y|,
+//   and resets a to 1; a failed trial halves a.  step[] holds a (-1 once g vanished).
 __global__ void refine_update_kernel(const RefineParams R) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= R.rows) return;
-    float st = R.init ? R.step0 : R.step[r];
+    float span[3], H[6];
+    for (int a = 0; a < 3; ++a) span[a] = R.hi[a] - R.lo[a];
+    float al = R.init ? 1.f : R.step[r];
     if (R.init) {
+        float gz[3];
         R.S[r] = R.trial_S[r];
         R.stack[r] = R.trial_stack[r];
-        for (int a = 0; a < 3; ++a) R.grad[r * 3 + a] = R.trial_grad[r * 3 + a];
-    } else if (R.judge && st > 0.f) {
-        if (R.trial_S[r] >= R.S[r]) {
-            R.S[r] = R.trial_S[r];
-            R.stack[r] = R.trial_stack[r];
-            for (int a = 0; a < 3; ++a) {
-                R.theta[r * 3 + a] = R.trial_theta[r * 3 + a];
-                R.grad[r * 3 + a] = R.trial_grad[r * 3 + a];
+        for (int a = 0; a < 3; ++a) {
+            R.grad[r * 3 + a] = R.trial_grad[r * 3 + a];
+            gz[a] = R.trial_grad[r * 3 + a] * span[a];
+        }
+        h_reset(H, gz, R.step0);
+    } else {
+        for (int i = 0; i < 6; ++i) H[i] = R.H[r * 6 + i];
+        if (R.judge && al > 0.f) {
+            if (R.trial_S[r] >= R.S[r]) {
+                float sv[3], yv[3], ss = 0.f, yy = 0.f, sy = 0.f;
+                for (int a = 0; a < 3; ++a) {
+                    sv[a] = (R.trial_theta[r * 3 + a] - R.lo[a]) / span[a] -
+                            (R.theta[r * 3 + a] - R.lo[a]) / span[a];
+                    yv[a] = R.grad[r * 3 + a] * span[a] - R.trial_grad[r * 3 + a] * span[a];
+                    ss = fmaf(sv[a], sv[a], ss);
+                    yy = fmaf(yv[a], yv[a], yy);
+                    sy = fmaf(sv[a], yv[a], sy);
+                }
+                if (sy > 1e-6f * sqrtf(ss) * sqrtf(yy)) {
+                    float u[3];
+                    h_mul(H, yv, u);
+                    const float rho = 1.f / sy;
+                    const float yu = yv[0] * u[0] + yv[1] * u[1] + yv[2] * u[2];
+                    const float c = rho + rho * rho * yu;
+                    const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+                    for (int k = 0; k < 6; ++k) {
+                        const int i = ii[k], j = jj[k];
+                        H[k] += -rho * (u[i] * sv[j] + sv[i] * u[j]) + c * sv[i] * sv[j];
+                    }
+                }
+                R.S[r] = R.trial_S[r];
+                R.stack[r] = R.trial_stack[r];
+                for (int a = 0; a < 3; ++a) {
+                    R.theta[r * 3 + a] = R.trial_theta[r * 3 + a];
+                    R.grad[r * 3 + a] = R.trial_grad[r * 3 + a];
+                }
+                al = 1.f;
+            } else {
+                al *= 0.5f;
             }
-        } else {
-            st *= 0.5f;
         }
     }
     if (R.propose) {
-        float gz[3], gn = 0.f;
-        for (int a = 0; a < 3; ++a) {
-            gz[a] = R.grad[r * 3 + a] * (R.hi[a] - R.lo[a]);
-            gn = fmaf(gz[a], gz[a], gn);
+        float gz[3], d[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < 3; ++a) gz[a] = R.grad[r * 3 + a] * span[a];
+        const float gn = sqrtf(gz[0] * gz[0] + gz[1] * gz[1] + gz[2] * gz[2]);
+        if (!(gn > 0.f)) al = -1.f;                  // stationary: stop
+        if (al > 0.f) {
+            h_mul(H, gz, d);
+            if (!(d[0] * gz[0] + d[1] * gz[1] + d[2] * gz[2] > 0.f)) {
+                h_reset(H, gz, R.step0);
+                h_mul(H, gz, d);
+            }
+            const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (dn > 0.25f)
+                for (int a = 0; a < 3; ++a) d[a] *= 0.25f / dn;
         }
-        gn = sqrtf(gn);
-        if (!(gn > 0.f)) st = -1.f;                  // stationary: stop
         for (int a = 0; a < 3; ++a) {
-            const float span = R.hi[a] - R.lo[a];
-            float z = (R.theta[r * 3 + a] - R.lo[a]) / span;
-            if (st > 0.f) z = fminf(fmaxf(z + st * gz[a] / gn, 0.f), 1.f);
-            R.trial_theta[r * 3 + a] = st > 0.f ? fmaf(z, span, R.lo[a]) : R.theta[r * 3 + a];
+            const float z = (R.theta[r * 3 + a] - R.lo[a]) / span[a];
+            const float zt = fminf(fmaxf(z + al * d[a], 0.f), 1.f);
+            R.trial_theta[r * 3 + a] = al > 0.f ? fmaf(zt, span[a], R.lo[a]) : R.theta[r * 3 + a];
         }
     }
-    R.step[r] = st;
+    for (int i = 0; i < 6; ++i) R.H[r * 6 + i] = H[i];
+    R.step[r] = al;
 }
 
 template <bool CRS, int W, bool GRAD>

@@ -77,6 +77,7 @@ struct RefineParams {
     const float* trial_grad;
     const float* trial_stack;
     float* step;
+    float* H;       // [rows][6] inverse curvature estimates (symmetric 3x3)
     float lo[3], hi[3];
     float step0;
     int judge, propose, init;
@@ -86,6 +87,14 @@ struct RefineParams {
 cudaError_t launch_search(const SearchParams& p, bool crs, int w, cudaStream_t stream);
 cudaError_t launch_eval(const EvalParams& p, bool crs, bool grad, int w, cudaStream_t s);
 cudaError_t launch_refine_update(const RefineParams& r, cudaStream_t s);
+int refine_run(const EvalParams& p0, float* theta, const float* lo3, const float* hi3,
+               int32_t steps, float step0, int32_t w, float* S_out, float* grad_out,
+               float* stack_out, void* workspace, int64_t rows, cudaStream_t s);
+int refine_check(const seis_gathers* d, const seis_aperture* ap, const float* theta,
+                 const float* lo3, const float* hi3, int32_t steps, float step0, int32_t w,
+                 const float* S_out, const float* grad_out, const float* stack_out,
+                 const void* workspace, size_t ws_bytes, size_t ws_needed, int64_t rows,
+                 EvalParams* p);
 int eval_tile_rows();
 
 // Batched search: one persistent launch over items (see seis_batch_semblance).

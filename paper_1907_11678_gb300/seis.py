@@ -80,6 +80,11 @@ def load_library(path: str | None = None):
             lib.seis_refine_workspace_size.restype = ctypes.c_size_t
             lib.crs_refine.argtypes = [vp, vp, vp, vp, vp, i32, f32, i32, vp, vp, vp, vp,
                                        ctypes.c_size_t, i64, vp]
+            lib.crs_top_starts.argtypes = [vp, i64, vp, i32, vp, i32, vp, i32, i32, vp, vp]
+            lib.seis_refine_multi_workspace_size.argtypes = [i64]
+            lib.seis_refine_multi_workspace_size.restype = ctypes.c_size_t
+            lib.crs_refine_multi.argtypes = [vp, vp, vp, i32, vp, vp, i32, f32, i32, vp, vp, vp,
+                                             vp, vp, ctypes.c_size_t, i64, vp]
             lib.seis_batch_workspace_size.argtypes = [i64]
             lib.seis_batch_workspace_size.restype = ctypes.c_size_t
             lib.seis_batch_semblance.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, i32,
@@ -92,7 +97,8 @@ def load_library(path: str | None = None):
                          "seis_set_search_variant", "seis_get_search_variant",
                          "seis_autotune_cmp", "seis_autotune_crs", "seis_autotune_save",
                          "seis_autotune_load", "seis_autotune_clear", "stack",
-                         "crs_semblance_grad", "crs_refine", "seis_batch_semblance",
+                         "crs_semblance_grad", "crs_refine", "crs_top_starts",
+                         "crs_refine_multi", "seis_batch_semblance",
                          "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -373,6 +379,48 @@ def crs_refine(g: Gathers, ap: "Aperture", ABC0: torch.Tensor, lo3, hi3, steps: 
                           _ptr(theta), lo, hi, int(steps), ctypes.c_float(step0), w, _ptr(S),
                           _ptr(grad), _ptr(st), ctypes.c_void_p(aligned),
                           workspace.numel() - (aligned - base), ap.rows, _stream_handle(stream)))
+    return dict(theta=theta, S=S, grad=grad, stack=st)
+
+
+def crs_top_starts(S_cube: torch.Tensor, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor,
+                   nstart: int, stream=None) -> torch.Tensor:
+    """The nstart best coarse candidates of every row of a CRS cube [rows, nA*nB*nC] as
+    operators [nstart, rows, 3] (include/seis.h: crs_top_starts)."""
+    lib = load_library()
+    S_cube = S_cube.contiguous()
+    rows = S_cube.shape[0]
+    A, B, C = (t.contiguous().float() for t in (A, B, C))
+    out = torch.empty((nstart, rows, 3), dtype=torch.float32, device=S_cube.device)
+    _check(lib.crs_top_starts(_ptr(S_cube), rows, _ptr(A), A.numel(), _ptr(B), B.numel(),
+                              _ptr(C), C.numel(), int(nstart), _ptr(out), _stream_handle(stream)))
+    return out
+
+
+def crs_refine_multi(g: Gathers, ap: "Aperture", starts: torch.Tensor, lo3, hi3,
+                     steps: int = 20, step0: float = 0.05, w: int = 11, stream=None,
+                     workspace=None) -> dict:
+    """crs_refine from each start [nstart, rows, 3], best S kept per row (include/seis.h:
+    crs_refine_multi).  Returns theta, S, grad, stack (device tensors)."""
+    lib = load_library()
+    dev = g.traces.device
+    starts = starts.detach().contiguous().float()
+    theta = torch.empty((ap.rows, 3), dtype=torch.float32, device=dev)
+    S = torch.empty(ap.rows, dtype=torch.float32, device=dev)
+    grad = torch.empty((ap.rows, 3), dtype=torch.float32, device=dev)
+    st = torch.empty(ap.rows, dtype=torch.float32, device=dev)
+    nbytes = lib.seis_refine_multi_workspace_size(ap.rows)
+    if workspace is None or workspace.numel() < nbytes + 256:
+        workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    lo = (ctypes.c_float * 3)(*[float(v) for v in lo3])
+    hi = (ctypes.c_float * 3)(*[float(v) for v in hi3])
+    _check(lib.crs_refine_multi(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
+                                _ptr(starts), int(starts.shape[0]), lo, hi, int(steps),
+                                ctypes.c_float(step0), w, _ptr(theta), _ptr(S), _ptr(grad),
+                                _ptr(st), ctypes.c_void_p(aligned),
+                                workspace.numel() - (aligned - base), ap.rows,
+                                _stream_handle(stream)))
     return dict(theta=theta, S=S, grad=grad, stack=st)
 
 

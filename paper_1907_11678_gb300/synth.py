@@ -239,6 +239,13 @@ BATCH_ITEM_DTYPE = np.dtype([("trace_begin", "<i8"), ("trace_end", "<i8"), ("out
                              ("c_off", "<i4"), ("nC", "<i4")])
 
 
+def score_cube(rows, ncand, levels=7, seed=9):
+    """Seeded scores in [0, 1) on a few levels (so rows hold many ties), float32
+    [rows, ncand]: input for the selection of refinement starts."""
+    rng = np.random.default_rng(seed)
+    return (rng.integers(0, levels, size=(rows, ncand)) / levels).astype(np.float32)
+
+
 def batch_workload(n_items=10000, seed=4, fold=(8, 120), ns=(1000, 4000), dts=(0.002, 0.004),
                    nc_range=(101, 201), crs_grid=(11, 11, 21), p_crs=0.5, snr=2.0,
                    max_dm=125.0, hmax=2500.0):

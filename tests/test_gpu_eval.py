@@ -127,18 +127,27 @@ def test_autograd_function_uses_adjoint(seis, line):
     torch.testing.assert_close(th.grad, wts[:, None] * dS, rtol=0, atol=0)
 
 
-def test_refine_monotone_and_consistent(seis, line):
+@pytest.fixture(scope="module")
+def coarse_starts(line):
+    """The oracle's coarse 7x7x11 search on the test line and its 4 best candidates per
+    row: the starting operators both sides refine from."""
     ds, g, ap = line
     lo, hi = _ranges()
     A = np.float32(np.linspace(lo[0], hi[0], 7)); B = np.float32(np.linspace(lo[1], hi[1], 7))
     C = np.float32(np.linspace(lo[2], hi[2], 11))
-    t = lambda a: torch.from_numpy(a).cuda()
-    coarse = seis.crs_semblance(g, ap, t(A), t(B), t(C), w=11)
-    th0 = coarse["best_ABC"]
+    ref = oracle.crs_semblance(ds, _nb_of(ap), A, B, C, want_cube=True)
+    return ref, oracle.top_starts(ref.S, A, B, C, 4)
+
+
+def test_refine_monotone_and_consistent(seis, line, coarse_starts):
+    ds, g, ap = line
+    lo, hi = _ranges()
+    coarse, starts = coarse_starts
+    th0 = torch.from_numpy(starts[0].astype(np.float32)).cuda()
+    S0 = seis.stack(g, ap, th0, w=11)["S"].cpu().numpy()
     r = seis.crs_refine(g, ap, th0, lo, hi, steps=20, step0=0.05, w=11)
     torch.cuda.synchronize()
     seis.device_status()
-    S0 = coarse["best_S"].cpu().numpy()
     S1 = r["S"].cpu().numpy()
     th1 = r["theta"].cpu().numpy()
     assert np.all(S1 >= S0 - 1e-6)
@@ -155,4 +164,42 @@ def test_refine_monotone_and_consistent(seis, line):
     close = np.abs(S1 - ref.S) <= 1e-3
     print(f"[parity] refine: gain {np.mean(S1 - S0):.4f}, |S_gpu - S_oracle| <= 1e-3 on "
           f"{close.mean():.3f} of rows, mean diff {np.mean(S1 - ref.S):+.2e}")
+    assert close.mean() >= 0.9
+
+
+def test_top_starts_exact(seis):
+    """Selection of refinement starts: integer work on a cube full of ties, bit-exact."""
+    rows, (nA, nB, nC) = 333, (5, 3, 7)
+    cube = synth.score_cube(rows, nA * nB * nC, levels=5, seed=17)
+    A = np.float32(np.linspace(-1, 1, nA)); B = np.float32(np.linspace(2, 3, nB))
+    C = np.float32(np.linspace(5, 9, nC))
+    t = lambda a: torch.from_numpy(a).cuda()
+    for k in (1, 6, nA * nB * nC):
+        got = seis.crs_top_starts(t(cube), t(A), t(B), t(C), k).cpu().numpy()
+        want = oracle.top_starts(cube, A, B, C, k).astype(np.float32)
+        np.testing.assert_array_equal(got, want)
+    with pytest.raises(seis.SeisError):
+        seis.crs_top_starts(t(cube), t(A), t(B), t(C), nA * nB * nC + 1)
+
+
+def test_refine_multi(seis, line, coarse_starts):
+    ds, g, ap = line
+    lo, hi = _ranges()
+    _, starts = coarse_starts
+    st = torch.from_numpy(starts.astype(np.float32)).cuda()
+    multi = seis.crs_refine_multi(g, ap, st, lo, hi, steps=20, step0=0.05, w=11)
+    single = seis.crs_refine(g, ap, st[0], lo, hi, steps=20, step0=0.05, w=11)
+    torch.cuda.synchronize()
+    seis.device_status()
+    Sm = multi["S"].cpu().numpy()
+    Ss = single["S"].cpu().numpy()
+    # start 0 runs the same arithmetic as the single refinement, so the best of all starts
+    # is never below it
+    assert np.all(Sm >= Ss)
+    thm = multi["theta"].cpu().numpy()
+    assert np.all(thm >= np.float32(lo) - 1e-12) and np.all(thm <= np.float32(hi) + 1e-12)
+    ref = oracle.crs_refine_multi(ds, _nb_of(ap), starts, lo, hi, steps=20, step0=0.05)
+    close = np.abs(Sm - ref.S) <= 1e-3
+    print(f"[parity] refine multi (4 starts): gain over one start {np.mean(Sm - Ss):.4f}, "
+          f"|S_gpu - S_oracle| <= 1e-3 on {close.mean():.3f} of rows")
     assert close.mean() >= 0.9

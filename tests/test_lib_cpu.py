@@ -117,3 +117,25 @@ def test_variant_selector(lib):
     assert lib.seis_set_search_variant(n) == -1
     assert lib.seis_set_search_variant(0) == 0 and lib.seis_get_search_variant() == 0
     assert lib.seis_set_search_variant(5) == 0
+
+
+def test_refine_starts_arguments_are_checked(lib):
+    fake = ctypes.c_void_p(16)               # never dereferenced: checks run first
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    # more starts than candidates
+    rc = lib.crs_top_starts(fake, i64(10), fake, i32(2), fake, i32(1), fake, i32(3), i32(7),
+                            fake, None)
+    assert rc == -1 and "nstart" in _err(lib)
+    rc = lib.crs_top_starts(fake, i64(10), fake, i32(2), fake, i32(1), fake, i32(3), i32(0),
+                            fake, None)
+    assert rc == -1
+    rc = lib.crs_top_starts(None, i64(10), fake, i32(2), fake, i32(1), fake, i32(3), i32(1),
+                            fake, None)
+    assert rc == -1 and "NULL" in _err(lib)
+    lib.seis_refine_multi_workspace_size.restype = ctypes.c_size_t
+    lib.seis_refine_workspace_size.restype = ctypes.c_size_t
+    assert lib.seis_refine_multi_workspace_size(i64(1000)) > lib.seis_refine_workspace_size(i64(1000))
+    rc = lib.crs_refine_multi(None, None, fake, i32(0), None, None, i32(20), ctypes.c_float(0.05),
+                              i32(11), fake, fake, fake, fake, fake, ctypes.c_size_t(0),
+                              i64(10), None)
+    assert rc == -1 and "nstart" in _err(lib)

@@ -340,6 +340,35 @@ def test_refine_invariants_and_exact_plane():
     assert r.S[1] > 0.999
 
 
+def test_top_starts_hand_worked():
+    """Candidates ordered by S descending, lowest index first on ties; cand = (ia*nB+ib)*nC+ic."""
+    S = np.array([[0.2, 0.5, 0.5, 0.1], [0.0, 0.0, 0.0, 0.0], [0.1, 0.2, 0.3, 0.4]])
+    A, B, C = [1.0, 2.0], [10.0], [100.0, 200.0]
+    got = oracle.top_starts(S, A, B, C, 3)
+    want = np.array([[[1, 10, 200], [1, 10, 100], [2, 10, 200]],
+                     [[2, 10, 100], [1, 10, 200], [2, 10, 100]],
+                     [[1, 10, 100], [2, 10, 100], [1, 10, 200]]], np.float64)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_refine_multi_keeps_best_start():
+    ds, (At, Bt, Ct) = _exact_plane()
+    nb = (np.array([0, len(ds["h"])], np.int64), np.arange(len(ds["h"]), dtype=np.int32),
+          np.float32([100.0]), np.array([0, 700], np.int64), np.float32([1.0 / 256]))
+    lo = np.array([0.0, -2.0 ** -16, 0.5 * Ct]); hi = np.array([2.0 * At, 2.0 ** -16, 2.0 * Ct])
+    rows = np.array([259, 260, 261])
+    starts = np.stack([np.tile([At * 1.6, 2.0 ** -18, Ct * 1.7], (3, 1)),
+                       np.tile([At * 1.02, 2.0 ** -19, Ct * 0.99], (3, 1))])
+    single = [oracle.crs_refine(ds, nb, s, lo, hi, steps=10, step0=0.01, rows=rows)
+              for s in starts]
+    multi = oracle.crs_refine_multi(ds, nb, starts, lo, hi, steps=10, step0=0.01, rows=rows)
+    np.testing.assert_array_equal(multi.S, np.maximum(single[0].S, single[1].S))
+    pick = np.where(single[1].S > single[0].S, 1, 0)
+    for r in range(3):
+        np.testing.assert_array_equal(multi.theta[r], single[pick[r]].theta[r])
+    assert multi.S[1] > 0.999          # the start next to the exact operator wins
+
+
 def test_invalid_arguments():
     ds = dataset([np.zeros(50)], [0.0], 0.004)
     with pytest.raises(ValueError):
