@@ -155,6 +155,17 @@ def neighbours(ds, central, apm):
     return off, tr, mc
 
 
+def aperture(ds, central, apm):
+    """The full neighbour description the CRS functions take: (nbr_off, nbr_trace, m_c,
+    out_off_c, dt_c), where the output rows of central i are those of its own gather."""
+    off, tr, mc = neighbours(ds, central, apm)
+    central = np.asarray(central, np.int64)
+    out_off = np.asarray(ds["out_off"], np.int64)
+    ns = out_off[central + 1] - out_off[central]
+    out_off_c = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    return off, tr, mc, out_off_c, np.asarray(ds["dt"], np.float32)[central]
+
+
 def _crs_common(ds, nb):
     off, tr, mc, out_off_c, dt_c = nb
     return (_c(ds["traces"], np.float32), _c(ds["trace_off"], np.int64), _c(ds["h"], np.float32),

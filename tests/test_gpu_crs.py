@@ -67,9 +67,10 @@ def test_crs_small_full_cube(seis):
     ds = synth.crs_line(9, 12, 300, 0.004, 0.0, 1500.0, 2, 1, 2.0, seed=41)
     g = seis.to_device(ds)
     ap = seis.crs_aperture(g, [3, 4, 5], 30.0)
+    nb = oracle.aperture(ds, [3, 4, 5], 30.0)
     A, B, C = _grids(5, 3, 7)
     got = _run(seis, g, ap, A, B, C)
-    ref = oracle.crs_semblance(ds, _nb_of(ap), A, B, C, want_cube=True)
+    ref = oracle.crs_semblance(ds, nb, A, B, C, want_cube=True)
     parity.check_cube(got["S"], ref, "crs-small")
     row_edge = (ref.edge != 0).any(axis=1)
     parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, "crs-small",
@@ -85,9 +86,10 @@ def test_crs_windows_and_ragged(seis, w):
     ds = synth.crs_line(7, 5, 170, 0.004, 0.0, 1200.0, 2, 1, 1.5, seed=50 + w)
     g = seis.to_device(ds)
     ap = seis.crs_aperture(g, [0, 3, 6], 25.0)
+    nb = oracle.aperture(ds, [0, 3, 6], 25.0)
     A, B, C = _grids(3, 2, 9)
     got = _run(seis, g, ap, A, B, C, w=w)
-    ref = oracle.crs_semblance(ds, _nb_of(ap), A, B, C, w=w, want_cube=True)
+    ref = oracle.crs_semblance(ds, nb, A, B, C, w=w, want_cube=True)
     parity.check_cube(got["S"], ref, f"crs-w{w}")
     parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, f"crs-w{w}",
                        row_edge=(ref.edge != 0).any(axis=1))
@@ -139,12 +141,13 @@ def test_crs_workload_slice_full_grid(seis):
     g = seis.to_device(ds)
     central = ds["central"][[0, 511, 1023]]
     ap = seis.crs_aperture(g, central, ds["apm"])
+    nb = oracle.aperture(ds, central, ds["apm"])
     assert int(ap.nbr_off[1] - ap.nbr_off[0]) == 1008
     A, B, C = _grids(21, 21, 41)
     got = _run(seis, g, ap, A, B, C, cube=False)
     rng = np.random.default_rng(1)
     rows = np.sort(rng.choice(ap.rows, 24, replace=False))
-    ref = oracle.crs_semblance(ds, _nb_of(ap), A, B, C, rows=rows, want_cube=True)
+    ref = oracle.crs_semblance(ds, nb, A, B, C, rows=rows, want_cube=True)
     rep = parity.check_picks(got["best_idx"][rows], got["best_S"][rows], got["stack"][rows],
                              ref, "crs-line", row_edge=(ref.edge != 0).any(axis=1))
     assert rep["pick_agree"] >= 0.9
