@@ -350,6 +350,14 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
     ap = seis.crs_aperture(g, central, ds["apm"])
     A, B, C = _crs_grids(torch, dev, synth, 21, 21, 41)
     inter = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 1500 * 21 * 21 * 41
+    # autotune on a 4-central slice in the same shape bucket (candidates, rows, fold)
+    if args.variant is None:
+        apt = seis.crs_aperture(g, ds["central"][:4], ds["apm"])
+        chosen, tune_ms = seis.autotune_crs(g, apt, A, B, C, w=W, reps=1)
+    else:
+        seis.autotune_clear()
+        seis.set_search_variant(args.variant)
+        chosen, tune_ms = args.variant, []
     seis.crs_semblance(g, ap, A, B, C, w=W)
     for _ in range(args.warmup - 1):
         seis.crs_semblance(g, ap, A, B, C, w=W)
@@ -367,7 +375,9 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
     return _simple_line("CRS " + METRIC, inter * world * W / (ms / 1e3), ms, args, world,
                         {"workload": f"crs-line: {len(central)} central CMPs of 1024, aperture "
                                      "+-10 CMPs (1008 traces), 1500 samples @4ms, 21x21x41, w=11",
-                         "intersections_per_step": inter * world},
+                         "intersections_per_step": inter * world, "kernel_variant": chosen,
+                         "kernel_variant_name": seis.search_variants()[chosen],
+                         "autotune_ms_4_centrals": [round(x, 3) for x in tune_ms]},
                         {"intersections_per_s": inter * world / (ms / 1e3),
                          "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
                                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": None}},

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
         for (;; ++s) {
             const int slot = s % kSlots;
             if (s >= kSlots && !sm.abort_flag) {
-                if (!mbar_wait_bounded(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
+                if (!mbar_wait_backoff(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
                     sm.abort_flag = 1;
                     record_status(P.status, kStatusTimeout);
                 }

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
         for (;; ++s) {
             const int slot = s % kSlots;
             if (s >= kSlots && !sm.abort_flag) {
-                if (!mbar_wait_bounded(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
+                if (!mbar_wait_backoff(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
                     sm.abort_flag = 1;
                     record_status(P.status, kStatusTimeout);
                 }

@@ -396,7 +396,8 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
 }
 
 // Check-free forms for traces on which every pair of the stage takes part: no mask test,
-// no select.  kk is clamped into the staged window only to keep every read inside it
+// no select, and for CRS no guard on sqrt(rad) + p, which the producer's test (rad >= 1,
+// p >= 1e-3 over the stage's box) keeps at or above 1.  kk is clamped into the staged window only to keep every read inside it
 // (rows past the owner's end and candidates past ncand land there; their sums are
 // discarded).
 template <bool CRS>
@@ -407,7 +408,7 @@ __device__ __forceinline__ void intersect_one_fast(float A, float B, float C, co
         const float a = A * tc.e;
         const float pp = nf + a;
         const float rr = fmaf(B, tc.g, C * tc.q);
-        D = fmaf(rr, rcp_fast(fmaxf(sqrt_fast(fmaf(pp, pp, rr)) + pp, 1e-30f)), a);
+        D = fmaf(rr, rcp_fast(sqrt_fast(fmaf(pp, pp, rr)) + pp), a);   // >= 1: no guard
     } else {
         const float cq = C * tc.q;
         D = cq * rcp_fast(sqrt_fast(nsq + cq) + nf);
@@ -434,7 +435,7 @@ __device__ __forceinline__ void intersect_pair_fast(f2_t A2, f2_t B2, f2_t C2, c
         const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), pp2);
         float sa, sb;
         up2(sum2, sa, sb);
-        D2 = fma2(rr2, pk2(rcp_fast(fmaxf(sa, 1e-30f)), rcp_fast(fmaxf(sb, 1e-30f))), a2);
+        D2 = fma2(rr2, pk2(rcp_fast(sa), rcp_fast(sb)), a2);      // sa, sb >= 1: no guard
     } else {
         const f2_t cq2 = mul2(C2, q2);
         const f2_t rad2 = add2(nsq2, cq2);
@@ -733,7 +734,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
         for (;; ++s) {
             const int slot = s % kSlots;
             if (s >= kSlots && !sm.abort_flag) {
-                if (!mbar_wait_bounded(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
+                if (!mbar_wait_backoff(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
                     sm.abort_flag = 1;
                     record_status(P.status, kStatusTimeout);
                 }

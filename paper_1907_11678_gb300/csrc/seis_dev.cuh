@@ -77,6 +77,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Wait of a warp that is usually early (a producer that runs ahead of its consumers by
+// several ring slots): sleep between tests with an exponential back-off up to ~1 us, so
+// that the waiting warp takes almost no issue slots from the warps doing the work.  Gives
+// up after limit_ns and returns false.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
+    if (mbar_test_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 64;
+    for (;;) {
+        __nanosleep(ns);
+        if (mbar_test_wait(bar, parity)) return true;
+        if (ns < 1024) ns <<= 1;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // 1-D bulk copy global -> shared through the TMA engine; completion is counted in bytes
 // on `bar`.  dst, src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
