@@ -391,6 +391,15 @@ def run_batch(args, torch, dist, seis, synth, rank, world, dev):
     ncand = np.where(items["kind"] == 1, items["nA"] * items["nB"] * items["nC"], items["nC"])
     inter = int(np.sum((items["trace_end"] - items["trace_begin"]) * items["rows"].astype(np.int64)
                        * ncand))
+    # autotune the batch kernel's tile shape on every 10th item (same size mix)
+    if args.variant is None:
+        bsub = seis.batch_to_device(items[::10], A, B, C, ds["out_rows"], dev)
+        chosen, tune_ms = seis.autotune_batch(g, bsub, w=W, reps=1)
+        del bsub
+    else:
+        seis.autotune_clear()
+        seis.set_search_variant(args.variant)
+        chosen, tune_ms = args.variant, []
     out = seis.batch_semblance(g, b, w=W, mode=0)
     torch.cuda.synchronize()
     seis.device_status()
@@ -416,7 +425,9 @@ def run_batch(args, torch, dist, seis, synth, rank, world, dev):
                         {"workload": f"batch: {args.items} items (CMP p=0.5: 101-201 C; CRS "
                                      "11x11x21), fold 8-120, 1000-4000 samples @2/4 ms, w=11, "
                                      "one persistent launch in a CUDA graph",
-                         "intersections_per_step": inter * world},
+                         "intersections_per_step": inter * world, "kernel_variant": chosen,
+                         "kernel_variant_name": seis.search_variants()[chosen],
+                         "autotune_ms_every_10th_item": [round(x, 3) for x in tune_ms]},
                         {"intersections_per_s": inter * world / (ms / 1e3),
                          "one_launch_per_item_ms": per_item_ms,
                          "speedup_vs_one_launch_per_item": per_item_ms / ms},

@@ -269,6 +269,20 @@ int seis_batch_semblance(const seis_gathers* d, const seis_batch_item* items, in
                          int32_t* best_idx, float* best_ABC, float* best_S, float* stack_out,
                          int64_t out_rows, void* workspace, size_t ws_bytes, void* stream);
 
+/* Autotuner of the batched search (no counterpart in the paper): runs the persistent
+ * launch of seis_batch_semblance once untimed and `reps` times between CUDA events with each
+ * variant the batch kernel is built for (0, 1, 3, 4, 9), records the fastest for the
+ * window length w (later seis_batch_semblance calls with that w use it) and returns it in
+ * *chosen (host, may be NULL).  ms_out (host, seis_search_variant_count() floats, may be
+ * NULL) receives each tried variant's mean time and -1 for the others.  SYNCHRONOUS.
+ * Arguments, outputs and errors as seis_batch_semblance (mode 0). */
+int seis_autotune_batch(const seis_gathers* d, const seis_batch_item* items, int64_t nitems,
+                        const float* poolA, int32_t sizeA, const float* poolB, int32_t sizeB,
+                        const float* poolC, int32_t sizeC, int32_t w, int32_t* best_idx,
+                        float* best_ABC, float* best_S, float* stack_out, int64_t out_rows,
+                        void* workspace, size_t ws_bytes, int32_t reps, int32_t* chosen,
+                        float* ms_out, void* stream);
+
 /* Allocation-free batched search (the paper has no counterpart: it concerns how this
  * library is called, not the method).  For callers that cannot allocate device memory
  * where they call the library -- a service running under a fixed device-memory budget, a

@@ -9,21 +9,33 @@
 
 namespace seis {
 
+cudaError_t launch_batch_v0(const BatchParams&, int, int, cudaStream_t);
 cudaError_t launch_batch_v1(const BatchParams&, int, int, cudaStream_t);
 cudaError_t launch_batch_v3(const BatchParams&, int, int, cudaStream_t);
+cudaError_t launch_batch_v4(const BatchParams&, int, int, cudaStream_t);
 cudaError_t launch_batch_v9(const BatchParams&, int, int, cudaStream_t);
 
-// The batch kernel is instantiated for three variants (its larger per-task state rules out
-// the 64-register shapes); any other choice maps to variant 3.
-int batch_variant_of(int v) { return (v == 1 || v == 3 || v == 9) ? v : 3; }
+// The batch kernel is instantiated for five of the search variants (its per-task state
+// costs registers, so the hybrid shapes are left out); any other choice maps to variant 3.
+static const int kBatchVariants[] = {0, 1, 3, 4, 9};
+int batch_variant_of(int v) {
+    for (int b : kBatchVariants)
+        if (b == v) return v;
+    return 3;
+}
 
 cudaError_t launch_batch(const BatchParams& p, int w, int grid, cudaStream_t s) {
     switch (batch_variant_of(p.variant)) {
+        case 0: return launch_batch_v0(p, w, grid, s);
         case 1: return launch_batch_v1(p, w, grid, s);
+        case 4: return launch_batch_v4(p, w, grid, s);
         case 9: return launch_batch_v9(p, w, grid, s);
         default: return launch_batch_v3(p, w, grid, s);
     }
 }
+
+// Tuning key of the batched search: one bucket per window length.
+static TuneKey batch_key(int w) { return TuneKey{2, w, 0, 0, 0}; }
 
 // One CTA: validate every item (an invalid one gets no tasks and sets the status bit),
 // prefix-sum the tiles of 32 rows into task_off, zero the work counter.
@@ -88,13 +100,14 @@ extern "C" size_t seis_batch_workspace_size(int64_t nitems) {
     return 256 + align256(((size_t)nitems + 1) * sizeof(int64_t));
 }
 
-extern "C" int seis_batch_semblance(const seis_gathers* d, const seis_batch_item* items,
-                                    int64_t nitems, const float* poolA, int32_t sizeA,
-                                    const float* poolB, int32_t sizeB, const float* poolC,
-                                    int32_t sizeC, int32_t w, int32_t mode, int32_t* best_idx,
-                                    float* best_ABC, float* best_S, float* stack_out,
-                                    int64_t out_rows, void* workspace, size_t ws_bytes,
-                                    void* stream) {
+namespace seis {
+
+// Checks the arguments of seis_batch_semblance and fills the launch parameters.
+static int batch_prepare(const seis_gathers* d, const seis_batch_item* items, int64_t nitems,
+                         const float* poolA, int32_t sizeA, const float* poolB, int32_t sizeB,
+                         const float* poolC, int32_t sizeC, int32_t w, int32_t mode,
+                         int32_t* best_idx, float* best_ABC, float* best_S, float* stack_out,
+                         int64_t out_rows, void* workspace, size_t ws_bytes, BatchParams* out) {
     if (!d || !d->traces || !d->trace_off || !d->half_offset)
         return fail(SEIS_EINVAL, "gathers descriptor or its trace arrays are NULL");
     if ((reinterpret_cast<uintptr_t>(d->traces) & 3u) != 0)
@@ -115,7 +128,6 @@ extern "C" int seis_batch_semblance(const seis_gathers* d, const seis_batch_item
         return fail(SEIS_EINVAL, "workspace of %zu bytes needed", seis_batch_workspace_size(nitems));
     if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
         return fail(SEIS_EINVAL, "workspace must be 256-byte aligned");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     BatchParams p{};
     p.traces = d->traces;
     p.trace_off = d->trace_off;
@@ -137,7 +149,13 @@ extern "C" int seis_batch_semblance(const seis_gathers* d, const seis_batch_item
     p.counter = static_cast<unsigned long long*>(workspace);
     p.task_off = reinterpret_cast<int64_t*>(static_cast<char*>(workspace) + 256);
     p.status = device_status_word();
-    p.variant = lookup_variant(make_tune_key(true, w, -1, 0, 0), default_variant());
+    p.variant = lookup_variant(batch_key(w), default_variant());
+    *out = p;
+    return SEIS_OK;
+}
+
+// Task table, then the persistent launch (mode 0) or one launch per item (mode 1).
+static int batch_run(BatchParams p, int32_t w, int32_t mode, int64_t out_rows, cudaStream_t s) {
     cudaError_t e = launch_batch_setup(p, out_rows, s);
     if (e != cudaSuccess) return cuda_fail(e, "batch setup");
     int dev = 0, sms = 0;
@@ -146,16 +164,16 @@ extern "C" int seis_batch_semblance(const seis_gathers* d, const seis_batch_item
         return cuda_fail(e, "batch");
     if (mode == 0) {
         p.item_begin = 0;
-        p.item_end = nitems;
+        p.item_end = p.nitems;
         if ((e = launch_batch(p, w, 2 * sms, s)) != cudaSuccess) return cuda_fail(e, "batch launch");
         return SEIS_OK;
     }
     // one launch per item: the task table is read back to size each launch
-    std::vector<int64_t> off((size_t)nitems + 1);
+    std::vector<int64_t> off((size_t)p.nitems + 1);
     e = cudaMemcpyAsync(off.data(), p.task_off, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "batch per-item");
-    for (int64_t i = 0; i < nitems; ++i) {
+    for (int64_t i = 0; i < p.nitems; ++i) {
         const int64_t tasks = off[i + 1] - off[i];
         if (tasks <= 0) continue;
         p.item_begin = i;
@@ -165,5 +183,68 @@ extern "C" int seis_batch_semblance(const seis_gathers* d, const seis_batch_item
         const int grid = (int)(tasks < 2 * sms ? tasks : 2 * sms);
         if ((e = launch_batch(p, w, grid, s)) != cudaSuccess) return cuda_fail(e, "batch launch");
     }
+    return SEIS_OK;
+}
+
+}  // namespace seis
+
+extern "C" int seis_batch_semblance(const seis_gathers* d, const seis_batch_item* items,
+                                    int64_t nitems, const float* poolA, int32_t sizeA,
+                                    const float* poolB, int32_t sizeB, const float* poolC,
+                                    int32_t sizeC, int32_t w, int32_t mode, int32_t* best_idx,
+                                    float* best_ABC, float* best_S, float* stack_out,
+                                    int64_t out_rows, void* workspace, size_t ws_bytes,
+                                    void* stream) {
+    BatchParams p;
+    int rc = batch_prepare(d, items, nitems, poolA, sizeA, poolB, sizeB, poolC, sizeC, w, mode,
+                           best_idx, best_ABC, best_S, stack_out, out_rows, workspace, ws_bytes,
+                           &p);
+    if (rc) return rc;
+    return batch_run(p, w, mode, out_rows, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int seis_autotune_batch(const seis_gathers* d, const seis_batch_item* items,
+                                   int64_t nitems, const float* poolA, int32_t sizeA,
+                                   const float* poolB, int32_t sizeB, const float* poolC,
+                                   int32_t sizeC, int32_t w, int32_t* best_idx, float* best_ABC,
+                                   float* best_S, float* stack_out, int64_t out_rows,
+                                   void* workspace, size_t ws_bytes, int32_t reps,
+                                   int32_t* chosen, float* ms_out, void* stream) {
+    BatchParams p;
+    int rc = batch_prepare(d, items, nitems, poolA, sizeA, poolB, sizeB, poolC, sizeC, w, 0,
+                           best_idx, best_ABC, best_S, stack_out, out_rows, workspace, ws_bytes,
+                           &p);
+    if (rc) return rc;
+    if (reps < 1) reps = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (ms_out)
+        for (int v = 0; v < search_variant_count(); ++v) ms_out[v] = -1.f;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(e, "batch autotune"); }
+    int best = -1;
+    float best_ms = 0.f;
+    for (int v : kBatchVariants) {
+        p.variant = v;
+        float ms = 0.f;
+        rc = batch_run(p, w, 0, out_rows, s);                  // untimed
+        if (!rc && (e = cudaEventRecord(e0, s)) != cudaSuccess) rc = cuda_fail(e, "batch autotune");
+        for (int r = 0; r < reps && !rc; ++r) rc = batch_run(p, w, 0, out_rows, s);
+        if (!rc && (e = cudaEventRecord(e1, s)) != cudaSuccess) rc = cuda_fail(e, "batch autotune");
+        if (!rc && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "batch autotune");
+        if (!rc && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+            rc = cuda_fail(e, "batch autotune");
+        if (rc) break;
+        ms /= (float)reps;
+        if (ms_out) ms_out[v] = ms;
+        if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    remember_variant(batch_key(w), best);
+    if (chosen) *chosen = best;
     return SEIS_OK;
 }

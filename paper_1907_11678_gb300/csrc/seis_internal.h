@@ -144,6 +144,7 @@ struct TuneKey {
     }
 };
 TuneKey make_tune_key(bool crs, int w, int ncand, int64_t max_rows, int64_t mean_fold);
+void remember_variant(const TuneKey& k, int v);
 int lookup_variant(const TuneKey& k, int fallback);
 int default_variant();
 

@@ -31,7 +31,7 @@ int lookup_variant(const TuneKey& k, int fallback) {
     return it == g_tuned.end() ? fallback : it->second;
 }
 
-static void remember(const TuneKey& k, int v) {
+void remember_variant(const TuneKey& k, int v) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[k] = v;
 }
@@ -65,7 +65,7 @@ static int tune(SearchParams p, bool crs, int w, int reps, cudaStream_t s, const
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    remember(key, best);
+    remember_variant(key, best);
     if (chosen) *chosen = best;
     return SEIS_OK;
 }
@@ -138,7 +138,7 @@ extern "C" int seis_autotune_load(const char* path) {
             return fail(SEIS_EINVAL, "malformed autotune entry in %s", path);
         if (v < 0 || v >= search_variant_count())
             return fail(SEIS_EINVAL, "variant %d out of range in %s", v, path);
-        remember(k, v);
+        remember_variant(k, v);
         ++loaded;
         ++p;
     }

@@ -90,6 +90,9 @@ def load_library(path: str | None = None):
             lib.seis_batch_semblance.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, i32,
                                                  vp, vp, vp, vp, i64, vp, ctypes.c_size_t, vp]
             lib.seis_selftest_wait_timeout.argtypes = [i32, vp]
+            lib.seis_autotune_batch.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, vp,
+                                                vp, vp, vp, i64, vp, ctypes.c_size_t, i32, vp,
+                                                vp, vp]
             lib.seis_autotune_save.argtypes = [ctypes.c_char_p]
             lib.seis_autotune_load.argtypes = [ctypes.c_char_p]
             for name in ("seis_device_status", "cmp_semblance", "crs_semblance",
@@ -98,7 +101,7 @@ def load_library(path: str | None = None):
                          "seis_autotune_cmp", "seis_autotune_crs", "seis_autotune_save",
                          "seis_autotune_load", "seis_autotune_clear", "stack",
                          "crs_semblance_grad", "crs_refine", "crs_top_starts",
-                         "crs_refine_multi", "seis_batch_semblance",
+                         "crs_refine_multi", "seis_batch_semblance", "seis_autotune_batch",
                          "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -489,6 +492,29 @@ def batch_semblance(g: Gathers, b: Batch, w: int = 11, mode: int = 0, stream=Non
         b.out_rows, ctypes.c_void_p(aligned), b.workspace.numel() - (aligned - base),
         _stream_handle(stream)))
     return out
+
+
+def autotune_batch(g: Gathers, b: Batch, w: int = 11, reps: int = 1, stream=None):
+    """Pick the batch kernel variant for window w by timing the persistent launch
+    (include/seis.h: seis_autotune_batch).  Returns (chosen, ms per variant or -1)."""
+    lib = load_library()
+    dev = g.traces.device
+    out = dict(best_idx=torch.empty(b.out_rows, dtype=torch.int32, device=dev),
+               best_ABC=torch.empty((b.out_rows, 3), dtype=torch.float32, device=dev),
+               best_S=torch.empty(b.out_rows, dtype=torch.float32, device=dev),
+               stack=torch.empty(b.out_rows, dtype=torch.float32, device=dev))
+    base = b.workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    nv = lib.seis_search_variant_count()
+    ms = (ctypes.c_float * nv)()
+    chosen = ctypes.c_int32(-1)
+    _check(lib.seis_autotune_batch(
+        ctypes.byref(g.descriptor()), _ptr(b.items), b.nitems, _ptr(b.poolA), int(b.poolA.numel()),
+        _ptr(b.poolB), int(b.poolB.numel()), _ptr(b.poolC), int(b.poolC.numel()), w,
+        _ptr(out["best_idx"]), _ptr(out["best_ABC"]), _ptr(out["best_S"]), _ptr(out["stack"]),
+        b.out_rows, ctypes.c_void_p(aligned), b.workspace.numel() - (aligned - base), int(reps),
+        ctypes.byref(chosen), ms, _stream_handle(stream)))
+    return int(chosen.value), list(ms)
 
 
 def selftest_wait_timeout(limit_us: int = 10000, stream=None) -> None:
