@@ -154,14 +154,26 @@ class ClockSampler:
                     reasons=sorted(reasons))
 
 
-def _profile_traffic(kernel_tag):
-    """DRAM traffic per unit (gather) from a committed ncu summary, if it was taken on the
-    current kernel source (hash match); else None."""
-    src = sorted(glob.glob(os.path.join(ROOT, "paper_1907_11678_gb300", "csrc", "*")))
+# the sources the search kernel is compiled from (its ncu counters stay valid while these
+# are unchanged)
+SEARCH_KERNEL_SOURCES = ("search_kernel.cuh", "seis_dev.cuh", "seis_internal.h",
+                         "search_dispatch.cu", "search_cmp_v*.cu", "search_crs_v*.cu")
+
+
+def _kernel_digest():
+    csrc = os.path.join(ROOT, "paper_1907_11678_gb300", "csrc")
     h = hashlib.sha256()
-    for f in src:
-        h.update(open(f, "rb").read())
-    digest = h.hexdigest()[:16]
+    for pat in SEARCH_KERNEL_SOURCES:
+        for f in sorted(glob.glob(os.path.join(csrc, pat))):
+            h.update(os.path.basename(f).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(kernel_tag, unit_key="dram_bytes_per_gather"):
+    """DRAM traffic per unit from a committed ncu summary, if it was taken on the current
+    search-kernel sources (hash match); else None."""
+    digest = _kernel_digest()
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
     if not os.path.exists(path):
         return None, digest
@@ -169,9 +181,9 @@ def _profile_traffic(kernel_tag):
         d = json.load(open(path))
     except Exception:
         return None, digest
-    if d.get("csrc_sha256_16") != digest:
+    if d.get("kernel_sources_sha256_16") != digest:
         return None, digest
-    return d.get("dram_bytes_per_gather"), digest
+    return d.get(unit_key), digest
 
 
 def _time_steps(torch, stream, fn, steps):
@@ -275,7 +287,7 @@ def run_cmp_line(args, torch, dist, seis, synth, rank, world, dev):
                      "flops_per_intersection": FLOPS_PER_INTERSECTION,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
                      "kernel": f"search_kernel<CMP, w=11, variant {chosen}>",
-                     "csrc_sha256_16": digest},
+                     "kernel_sources_sha256_16": digest},
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk,
@@ -372,6 +384,15 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
     ach = inter * FLOPS_PER_INTERSECTION / (np.mean(kern) / 1e3) / 1e12
+    # unique bytes: the traces of every CMP some aperture reaches, read once, plus 6 output
+    # values per row; DRAM traffic scaled from the committed capture by the CMPs read
+    tr_ids = ap.nbr_trace[:int(ap.nbr_off[-1])].cpu().numpy()
+    cmps = np.unique(np.searchsorted(ds["gather_off"], tr_ids, side="right") - 1)
+    cmp_bytes = int(sum(ds["trace_off"][ds["gather_off"][c + 1]] - ds["trace_off"][ds["gather_off"][c]]
+                        for c in cmps)) * 4
+    alg_bytes = cmp_bytes + ap.rows * 6 * 4
+    tper, digest = _profile_traffic("search_kernel_crs_line", "dram_bytes_per_cmp_read")
+    traffic = None if tper is None else tper * len(cmps)
     return _simple_line("CRS " + METRIC, inter * world * W / (ms / 1e3), ms, args, world,
                         {"workload": f"crs-line: {len(central)} central CMPs of 1024, aperture "
                                      "+-10 CMPs (1008 traces), 1500 samples @4ms, 21x21x41, w=11",
@@ -380,7 +401,13 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
                          "autotune_ms_4_centrals": [round(x, 3) for x in tune_ms]},
                         {"intersections_per_s": inter * world / (ms / 1e3),
                          "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
-                                      "unit": "TFLOP/s", "frac": ach / peak, "traffic": None}},
+                                      "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                                      "algorithmic_bytes": alg_bytes,
+                                      "flops_per_intersection": FLOPS_PER_INTERSECTION,
+                                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x "
+                                                    f"{SM_MAX_MHZ:g} MHz",
+                                      "kernel": f"search_kernel<CRS, w=11, variant {chosen}>",
+                                      "kernel_sources_sha256_16": digest}},
                         clk, args.steps)
 
 
