@@ -534,6 +534,86 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
                         clk, launches)
 
 
+# The paper's Table 1 shapes: (shape, CMP gathers, CRS central CMPs, CRS aperture in CMPs
+# per side).  Gathers are chosen so that each CMP input is about 1 GB (larger than L2);
+# the CRS apertures hold 1260 (fold 60) or 5000 (fold 1000) traces, and the centrals give
+# CTA counts (centrals x tiles of 32 rows) just under a whole number of waves of the 304
+# resident CTA slots (1152 = 3.8 waves, 884 = 2.9, 288 = 0.95, 572 = 1.9).
+PAPER_RUNS = [("data1/data2", 8192, 64, 10), ("data3/data4", 2048, 17, 10),
+              ("data5/data6", 512, 16, 2), ("data7/data8", 128, 11, 2)]
+
+
+def run_paper(args, torch, dist, seis, synth, rank, world, dev):
+    C = _candidates()
+    Cd = torch.from_numpy(C).to(dev)
+    A, B, Cc = _crs_grids(torch, dev, synth, 21, 21, 41)
+    ncrs = 21 * 21 * 41
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    stream = torch.cuda.current_stream()
+    entries = []
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        seis.device_status()
+        kern, total = _time_steps(torch, stream, fn, args.steps)
+        seis.device_status()
+        return float(np.mean(kern)), total / args.steps
+
+    def entry(shape, method, units, fold, ns, ncand, inter, kern_ms, ms, chosen):
+        return {"dataset": shape, "method": method, **units, "fold": fold, "samples": ns,
+                "candidates": ncand, "intersections": inter, "ms": ms,
+                "intersections_per_s": inter / (ms / 1e3),
+                "trace_samples_per_s": inter * W / (ms / 1e3),
+                "roofline_frac": inter * FLOPS_PER_INTERSECTION / (kern_ms / 1e3) / 1e12 / peak,
+                "kernel_variant": chosen}
+
+    for shape, G, ncen, pad in PAPER_RUNS:
+        fold, ns = synth.PAPER_SHAPES[shape]
+        ds = synth.workload_paper_cmp(shape, G, seed=6 + 1000 * rank)
+        g = seis.to_device(ds, dev)
+        if args.variant is None:
+            sub = synth.workload_paper_cmp(shape, max(16, G // 8), seed=99)
+            chosen, _ = seis.autotune_cmp(seis.to_device(sub, dev), Cd, w=W, reps=1)
+        else:
+            seis.set_search_variant(args.variant)
+            chosen = args.variant
+        out = seis.cmp_semblance(g, Cd, w=W)
+        kern, ms = timed(lambda: seis.cmp_semblance(g, Cd, w=W, out=out))
+        entries.append(entry(shape, "CMP", {"gathers": G}, fold, ns, NC, G * fold * ns * NC,
+                             kern, ms, chosen))
+        del g, out, ds
+        ds = synth.workload_paper_crs(shape, ncen, pad, seed=7 + 1000 * rank)
+        g = seis.to_device(ds, dev)
+        ap = seis.crs_aperture(g, ds["central"], ds["apm"])
+        if args.variant is None:
+            apt = seis.crs_aperture(g, ds["central"][:2], ds["apm"])
+            chosen, _ = seis.autotune_crs(g, apt, A, B, Cc, w=W, reps=1)
+        inter = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * ns * ncrs
+        kern, ms = timed(lambda: seis.crs_semblance(g, ap, A, B, Cc, w=W))
+        entries.append(entry(shape, "CRS", {"central_cmps": ncen, "aperture_traces":
+                                            int(ap.nbr_off[1] - ap.nbr_off[0])},
+                             fold, ns, ncrs, inter, kern, ms, chosen))
+        del g, ap, ds
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    tot_inter = sum(e["intersections"] for e in entries)
+    tot_ms = sum(e["ms"] for e in entries)
+    return _simple_line("paper-shaped CMP+CRS " + METRIC, tot_inter * W / (tot_ms / 1e3), tot_ms,
+                        args, world,
+                        {"workload": "the paper's Table 1 shapes (fold 60/1000 x 550/1650 "
+                                     "samples @4 ms), CMP 201 C and CRS 21x21x41, w=11; one "
+                                     "step = every dataset once",
+                         "l2": "CMP inputs ~1 GB (larger than L2); CRS apertures re-read "
+                               "from L2 by design"},
+                        {"intersections_per_s": tot_inter / (tot_ms / 1e3),
+                         "datasets": entries}, clk, len(entries) * args.steps)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -547,7 +627,7 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     seis_build.build()
     fn = {"cmp-line": run_cmp_line, "crs-line": run_crs_line, "batch": run_batch,
-          "refine": run_refine}[args.workload]
+          "refine": run_refine, "paper": run_paper}[args.workload]
     line = fn(args, torch, dist, seis, synth, rank, world, dev)
     if world > 1:
         dist.barrier()
@@ -603,7 +683,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cmp-line",
-                    choices=["cmp-line", "crs-line", "batch", "refine"])
+                    choices=["cmp-line", "crs-line", "batch", "refine", "paper"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)

@@ -221,6 +221,33 @@ def workload_crs_refine(seed=5, n_central=512, pad=8):
     return ds
 
 
+# The paper's Table 1 shapes (fold, samples per trace).  Its "dt" column (220 / 240) is not
+# a sampling interval and is not used, so data1 and data2 (and each later pair) share one
+# shape; all are sampled at 4 ms here.
+PAPER_SHAPES = {"data1/data2": (60, 550), "data3/data4": (60, 1650),
+                "data5/data6": (1000, 550), "data7/data8": (1000, 1650)}
+
+
+def workload_paper_cmp(shape, G, seed=6):
+    """G CMP gathers of a Table 1 shape on a line, h 25..3000 m, 4 ms, 6 events with a
+    lateral velocity gradient of 0.5 m/s per CMP, SNR 1."""
+    fold, ns = PAPER_SHAPES[shape]
+    return cmp_line(G, fold, ns, 0.004, 25.0, 3000.0, 6, 1.0, seed,
+                    v_range=(2550.0, 3450.0), v_gradient=0.5)
+
+
+def workload_paper_crs(shape, n_central, pad, seed=7):
+    """n_central central CMPs of a Table 1 shape plus pad CMPs each side at 12.5 m (the
+    aperture reaches pad CMPs per side), h 0..2400 m, 4 ms; planes and diffractors, SNR 2."""
+    fold, ns = PAPER_SHAPES[shape]
+    rng = np.random.default_rng(seed + 1000)
+    ds = crs_line(n_central + 2 * pad, fold, ns, 0.004, 0.0, 2400.0,
+                  int(rng.integers(3, 5)), int(rng.integers(2, 4)), 2.0, seed)
+    ds["central"] = np.arange(pad, pad + n_central, dtype=np.int32)
+    ds["apm"] = pad * 12.5
+    return ds
+
+
 def crs_ranges(max_dip_deg=20.0, vmin=1500.0, vlo=1400.0, vhi=4500.0):
     """(lo, hi) of A, B, C for the CRS grids: A = +-2 sin(dip)/vmin, B = +-4/vlo^2,
     C = 4/v^2 over [vlo, vhi]."""

@@ -132,3 +132,13 @@ def test_cmp_line_full_size_sampled(seis):
                              row_edge=row_edge)
     assert rep["pick_agree"] > 0.98
     assert np.all(got["best_S"] >= 0) and np.all(got["best_S"] <= 1.0 + 1e-5)
+
+
+@pytest.mark.parametrize("shape", list(synth.PAPER_SHAPES))
+def test_paper_table1_shapes(seis, shape):
+    """Two gathers of each of the paper's Table 1 shapes (fold 60 / 1000 x 550 / 1650
+    samples): fold 1000 streams 32 stages of traces per candidate pass."""
+    fold, ns = synth.PAPER_SHAPES[shape]
+    ds = synth.cmp_line(2, fold, ns, 0.004, 25.0, 3000.0, 4, 1.0, seed=300 + fold + ns,
+                        v_range=(2550.0, 3450.0))
+    _check_all(seis, ds, _grid(23), label=f"cmp {shape}")

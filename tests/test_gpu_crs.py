@@ -151,3 +151,20 @@ def test_crs_workload_slice_full_grid(seis):
     rep = parity.check_picks(got["best_idx"][rows], got["best_S"][rows], got["stack"][rows],
                              ref, "crs-line", row_edge=(ref.edge != 0).any(axis=1))
     assert rep["pick_agree"] >= 0.9
+
+
+@pytest.mark.parametrize("shape", ["data1/data2", "data7/data8"])
+def test_crs_paper_table1_shapes(seis, shape):
+    """A central CMP of the paper's smallest and largest Table 1 shapes, aperture +-1 CMP
+    (180 or 3000 traces)."""
+    fold, ns = synth.PAPER_SHAPES[shape]
+    ds = synth.crs_line(3, fold, ns, 0.004, 0.0, 2400.0, 2, 1, 2.0, seed=310 + fold)
+    g = seis.to_device(ds)
+    ap = seis.crs_aperture(g, [1], 12.5)
+    nb = oracle.aperture(ds, [1], 12.5)
+    A, B, C = _grids(3, 3, 5)
+    got = _run(seis, g, ap, A, B, C)
+    ref = oracle.crs_semblance(ds, nb, A, B, C, want_cube=True)
+    parity.check_cube(got["S"], ref, f"crs {shape}")
+    parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, f"crs {shape}",
+                       row_edge=(ref.edge != 0).any(axis=1))
