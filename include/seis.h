@@ -161,6 +161,15 @@ int seis_crs_aperture(const seis_gathers* d, const int32_t* central, int64_t n_c
                       int64_t* total_entries, int64_t* total_rows, int32_t* max_rows,
                       void* stream);
 
+/* As seis_crs_aperture, keeping only the traces with |half_offset| <= hmax (hmax >= 0; 0
+ * keeps the zero-offset traces), e.g. for the zero-offset stage of crs_pragmatic.  Errors as
+ * seis_crs_aperture, and SEIS_EINVAL for hmax < 0 or NaN. */
+int seis_crs_aperture_offset(const seis_gathers* d, const int32_t* central, int64_t n_central,
+                             float apm, float hmax, int64_t* nbr_off, int32_t* nbr_trace,
+                             int64_t capacity, float* m_c, int64_t* out_off, float* dt_c,
+                             int64_t* total_entries, int64_t* total_rows, int32_t* max_rows,
+                             void* stream);
+
 /* CRS semblance search -- Section 2.2, Section 3.5 (aperture), Eq. 1, Algorithm 1.
  * Candidates are the flattened grid cand = (ia*nB + ib)*nC + ic of A[nA] (s/m),
  * B[nB] (s^2/m^2), C[nC] (s^2/m^2); trace i of the aperture of central c is intersected
@@ -232,6 +241,24 @@ int crs_refine_multi(const seis_gathers* d, const seis_aperture* ap, const float
                      float step0, int32_t w, float* ABC_out, float* S_out, float* grad_out,
                      float* stack_out, void* workspace, size_t ws_bytes, int64_t rows,
                      void* stream);
+
+/* CRS operator by two small searches instead of the dense grid (not in the paper, which
+ * searches the dense A x B x C grid of Section 2.2): C from the central CMP's own traces
+ * (ap_cmp: apm = 0, so dm = 0 and the traveltime is the CMP one of Section 2.1; A = B = 0),
+ * then A and B from the zero-offset traces of the aperture (ap_zo: seis_crs_aperture_offset
+ * with a small hmax; the C term is taken at the single value c_zo and vanishes where h = 0),
+ * then S and the stack of the combined operator (A, B from the second search, C from the
+ * first) over the full aperture ap_full, as stack() computes them.  The three apertures
+ * describe the same central CDPs (same n_central and rows).  Outputs best_ABC [rows][3],
+ * best_S, stack_out [rows] (device).  workspace: seis_pragmatic_workspace_size(rows) bytes,
+ * 256-byte aligned, caller-owned.  Asynchronous (two searches, the stack and two small
+ * kernels on stream).  Errors: SEIS_EINVAL, SEIS_ECUDA. */
+size_t seis_pragmatic_workspace_size(int64_t rows);
+int crs_pragmatic(const seis_gathers* d, const seis_aperture* ap_full,
+                  const seis_aperture* ap_cmp, const seis_aperture* ap_zo, const float* A,
+                  int32_t nA, const float* B, int32_t nB, const float* C, int32_t nC, float c_zo,
+                  int32_t w, float* best_ABC, float* best_S, float* stack_out, void* workspace,
+                  size_t ws_bytes, int64_t rows, void* stream);
 
 /* Batched search (no counterpart in the paper: its CGs take one CDP per task, Section 3.5;
  * here thousands of uneven CMP gathers and CRS supergathers run in ONE persistent launch

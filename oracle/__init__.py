@@ -283,6 +283,41 @@ def crs_refine_multi(ds, nb, starts, lo3, hi3, steps=20, step0=0.05, w=11, rows=
     return best
 
 
+def offset_limited(ds, nb, hmax):
+    """The neighbour description nb restricted to traces with |h| <= hmax (plain filter of
+    each central's list, order kept)."""
+    off, tr, mc, out_off_c, dt_c = nb
+    h = np.asarray(ds["h"], np.float32)
+    new_off, new_tr = [0], []
+    for c in range(len(off) - 1):
+        t = np.asarray(tr[off[c]:off[c + 1]])
+        keep = t[np.abs(h[t]) <= np.float32(hmax)]
+        new_tr.append(keep)
+        new_off.append(new_off[-1] + len(keep))
+    tr2 = np.concatenate(new_tr).astype(np.int32) if new_tr else np.zeros(0, np.int32)
+    return np.asarray(new_off, np.int64), tr2, mc, out_off_c, dt_c
+
+
+def crs_pragmatic(ds, central, apm, hzo, A, B, C, c_zo, w=11, nthreads=0) -> Result:
+    """CRS operator by two small searches (not in the paper): C from the central CMP's own
+    traces (dm = 0, A = B = 0: the CMP traveltime of Section 2.1), then A, B from the
+    aperture's traces with |h| <= hzo at C = c_zo, then S and stack of the combined
+    operator over the full aperture (Eq. 1, Algorithm 1).  Also returns each search's
+    best / second-best S for the pick-parity waiver."""
+    A = np.asarray(A); B = np.asarray(B); C = np.asarray(C)
+    nb_full = aperture(ds, central, apm)
+    nb_cmp = aperture(ds, central, 0.0)
+    nb_zo = offset_limited(ds, nb_full, hzo)
+    r1 = crs_semblance(ds, nb_cmp, [0.0], [0.0], C, w=w, want_cube=True, nthreads=nthreads)
+    r2 = crs_semblance(ds, nb_zo, A, B, [c_zo], w=w, want_cube=True, nthreads=nthreads)
+    theta = np.stack([A[r2.best_idx // len(B)], B[r2.best_idx % len(B)],
+                      C[r1.best_idx]], 1).astype(np.float64)
+    e = crs_eval(ds, nb_full, theta, w=w, nthreads=nthreads)
+    return Result(theta=theta, S=e.S, stack=e.stack, N=e.N, knot=e.knot,
+                  gap_cmp=r1.best_S - r1.second_S, gap_zo=r2.best_S - r2.second_S,
+                  edge_cmp=(r1.edge != 0).any(axis=1), edge_zo=(r2.edge != 0).any(axis=1))
+
+
 def cmp_as_crs(ds, gathers=None):
     """Neighbour description that makes each gather its own CRS 'aperture' (dm = 0
     when all traces of a gather share one midpoint); used by the reduction tests."""

@@ -1,5 +1,6 @@
 // seis_api.cu -- the C ABI of libseis (declared in include/seis.h): argument checks,
 // error reporting, the device status word, and the CRS aperture build.
+#include <cmath>
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstdarg>
@@ -212,11 +213,12 @@ namespace seis {
 
 // One CTA per central CDP: validate it (count -1 if the index is out of range or the
 // gather is empty), record its midpoint, rows and dt, and count the traces inside its
-// aperture (|m_i - m_c| <= apm in FP64, inclusive).
-__global__ void aperture_count_kernel(const float* m, const int64_t* gather_off,
+// aperture (|m_i - m_c| <= apm in FP64, inclusive, and |h_i| <= hmax).
+__global__ void aperture_count_kernel(const float* m, const float* h, const int64_t* gather_off,
                                       const int64_t* out_off, const float* dt, int64_t ngathers,
                                       int64_t ntraces, const int32_t* central, float apm,
-                                      int64_t* counts, float* m_c, int64_t* rows, float* dt_c) {
+                                      float hmax, int64_t* counts, float* m_c, int64_t* rows,
+                                      float* dt_c) {
     const int64_t c = blockIdx.x;
     const int32_t g = central[c];
     __shared__ unsigned long long part[256];
@@ -227,7 +229,8 @@ __global__ void aperture_count_kernel(const float* m, const int64_t* gather_off,
     const float mg = m[gather_off[g]];
     unsigned long long cnt = 0;
     for (int64_t i = threadIdx.x; i < ntraces; i += blockDim.x)
-        cnt += (fabs((double)m[i] - (double)mg) <= (double)apm) ? 1ull : 0ull;
+        cnt += (fabs((double)m[i] - (double)mg) <= (double)apm && fabsf(h[i]) <= hmax) ? 1ull
+                                                                                       : 0ull;
     part[threadIdx.x] = cnt;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
@@ -243,8 +246,9 @@ __global__ void aperture_count_kernel(const float* m, const int64_t* gather_off,
 }
 
 // One CTA per central CDP: ordered compaction of the aperture's trace indices.
-__global__ void aperture_fill_kernel(const float* m, int64_t ntraces, const int64_t* nbr_off,
-                                     const float* m_c, float apm, int32_t* nbr_trace) {
+__global__ void aperture_fill_kernel(const float* m, const float* h, int64_t ntraces,
+                                     const int64_t* nbr_off, const float* m_c, float apm,
+                                     float hmax, int32_t* nbr_trace) {
     const int64_t c = blockIdx.x;
     const double mg = (double)m_c[c];
     __shared__ int wsum[8];
@@ -253,7 +257,8 @@ __global__ void aperture_fill_kernel(const float* m, int64_t ntraces, const int6
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t i0 = 0; i0 < ntraces; i0 += 256) {
         const int64_t i = i0 + threadIdx.x;
-        const bool in = i < ntraces && fabs((double)m[i] - mg) <= (double)apm;
+        const bool in = i < ntraces && fabs((double)m[i] - mg) <= (double)apm &&
+                        fabsf(h[i]) <= hmax;
         const unsigned bal = __ballot_sync(0xffffffffu, in);
         if (lane == 0) wsum[warp] = __popc(bal);
         __syncthreads();
@@ -271,23 +276,26 @@ __global__ void aperture_fill_kernel(const float* m, int64_t ntraces, const int6
 
 }  // namespace seis
 
-extern "C" int seis_crs_aperture(const seis_gathers* d, const int32_t* central, int64_t n_central,
-                                 float apm, int64_t* nbr_off, int32_t* nbr_trace, int64_t capacity,
-                                 float* m_c, int64_t* out_off, float* dt_c, int64_t* total_entries,
-                                 int64_t* total_rows, int32_t* max_rows, void* stream) {
+static int crs_aperture_impl(const seis_gathers* d, const int32_t* central, int64_t n_central,
+                             float apm, float hmax, int64_t* nbr_off, int32_t* nbr_trace,
+                             int64_t capacity, float* m_c, int64_t* out_off, float* dt_c,
+                             int64_t* total_entries, int64_t* total_rows, int32_t* max_rows,
+                             void* stream) {
     int rc = check_gathers(d, true);
     if (rc) return rc;
     if (!central || n_central < 1) return fail(SEIS_EINVAL, "central must be non-NULL, n >= 1");
     if (!(apm >= 0.f)) return fail(SEIS_EINVAL, "apm must be >= 0");
+    if (!(hmax >= 0.f)) return fail(SEIS_EINVAL, "hmax must be >= 0");
     if (!nbr_off || !m_c || !out_off || !dt_c) return fail(SEIS_EINVAL, "an output array is NULL");
     if (n_central > INT32_MAX) return fail(SEIS_EINVAL, "too many centrals");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t n = n_central;
     cudaError_t e;
     // counts -> nbr_off[1..n], rows -> out_off[1..n], prefix sums on the host.
-    aperture_count_kernel<<<(unsigned)n, 256, 0, s>>>(d->midpoint, d->gather_off, d->out_off, d->dt,
-                                                      d->ngathers, d->ntraces, central, apm,
-                                                      nbr_off + 1, m_c, out_off + 1, dt_c);
+    aperture_count_kernel<<<(unsigned)n, 256, 0, s>>>(d->midpoint, d->half_offset, d->gather_off,
+                                                      d->out_off, d->dt, d->ngathers, d->ntraces,
+                                                      central, apm, hmax, nbr_off + 1, m_c,
+                                                      out_off + 1, dt_c);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "aperture count");
     std::vector<int64_t> cnt(n + 1), rows(n + 1);
     e = cudaMemcpyAsync(cnt.data() + 1, nbr_off + 1, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -316,13 +324,31 @@ extern "C" int seis_crs_aperture(const seis_gathers* d, const int32_t* central, 
             return fail(SEIS_EINVAL, "nbr_trace capacity %lld < %lld entries", (long long)capacity,
                         (long long)cnt[n]);
         }
-        aperture_fill_kernel<<<(unsigned)n, 256, 0, s>>>(d->midpoint, d->ntraces, nbr_off, m_c, apm,
-                                                         nbr_trace);
+        aperture_fill_kernel<<<(unsigned)n, 256, 0, s>>>(d->midpoint, d->half_offset, d->ntraces,
+                                                         nbr_off, m_c, apm, hmax, nbr_trace);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "aperture fill");
     }
     e = cudaStreamSynchronize(s);   // host vectors above are released on return
     if (e != cudaSuccess) return cuda_fail(e, "seis_crs_aperture");
     return SEIS_OK;
+}
+
+extern "C" int seis_crs_aperture(const seis_gathers* d, const int32_t* central, int64_t n_central,
+                                 float apm, int64_t* nbr_off, int32_t* nbr_trace, int64_t capacity,
+                                 float* m_c, int64_t* out_off, float* dt_c, int64_t* total_entries,
+                                 int64_t* total_rows, int32_t* max_rows, void* stream) {
+    return crs_aperture_impl(d, central, n_central, apm, INFINITY, nbr_off, nbr_trace, capacity,
+                             m_c, out_off, dt_c, total_entries, total_rows, max_rows, stream);
+}
+
+extern "C" int seis_crs_aperture_offset(const seis_gathers* d, const int32_t* central,
+                                        int64_t n_central, float apm, float hmax,
+                                        int64_t* nbr_off, int32_t* nbr_trace, int64_t capacity,
+                                        float* m_c, int64_t* out_off, float* dt_c,
+                                        int64_t* total_entries, int64_t* total_rows,
+                                        int32_t* max_rows, void* stream) {
+    return crs_aperture_impl(d, central, n_central, apm, hmax, nbr_off, nbr_trace, capacity,
+                             m_c, out_off, dt_c, total_entries, total_rows, max_rows, stream);
 }
 
 // ------------------------------------------------------------------ wait self-test ----

@@ -85,6 +85,12 @@ def load_library(path: str | None = None):
             lib.seis_refine_multi_workspace_size.restype = ctypes.c_size_t
             lib.crs_refine_multi.argtypes = [vp, vp, vp, i32, vp, vp, i32, f32, i32, vp, vp, vp,
                                              vp, vp, ctypes.c_size_t, i64, vp]
+            lib.seis_crs_aperture_offset.argtypes = [vp, vp, i64, f32, f32, vp, vp, i64, vp, vp,
+                                                     vp, vp, vp, vp, vp]
+            lib.seis_pragmatic_workspace_size.argtypes = [i64]
+            lib.seis_pragmatic_workspace_size.restype = ctypes.c_size_t
+            lib.crs_pragmatic.argtypes = [vp, vp, vp, vp, vp, i32, vp, i32, vp, i32, f32, i32, vp,
+                                          vp, vp, vp, ctypes.c_size_t, i64, vp]
             lib.seis_batch_workspace_size.argtypes = [i64]
             lib.seis_batch_workspace_size.restype = ctypes.c_size_t
             lib.seis_batch_semblance.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, i32,
@@ -102,6 +108,7 @@ def load_library(path: str | None = None):
                          "seis_autotune_load", "seis_autotune_clear", "stack",
                          "crs_semblance_grad", "crs_refine", "crs_top_starts",
                          "crs_refine_multi", "seis_batch_semblance", "seis_autotune_batch",
+                         "seis_crs_aperture_offset", "crs_pragmatic",
                          "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -224,8 +231,10 @@ class Aperture:
         return self._desc
 
 
-def crs_aperture(g: Gathers, central, apm: float, stream=None) -> Aperture:
-    """Build the CRS apertures of the central gathers (include/seis.h: seis_crs_aperture)."""
+def crs_aperture(g: Gathers, central, apm: float, hmax: float | None = None,
+                 stream=None) -> Aperture:
+    """Build the CRS apertures of the central gathers (include/seis.h: seis_crs_aperture, or
+    seis_crs_aperture_offset when hmax is given: only traces with |h| <= hmax)."""
     lib = load_library()
     dev = g.traces.device
     central = torch.as_tensor(np.asarray(central, np.int32)).to(dev)
@@ -238,12 +247,18 @@ def crs_aperture(g: Gathers, central, apm: float, stream=None) -> Aperture:
     rows = ctypes.c_int64(0)
     mr = ctypes.c_int32(0)
     sh = _stream_handle(stream)
-    args = (ctypes.byref(g.descriptor()), _ptr(central), n, ctypes.c_float(apm), _ptr(nbr_off))
-    _check(lib.seis_crs_aperture(*args, None, 0, _ptr(m_c), _ptr(out_off), _ptr(dt_c),
-                                 ctypes.byref(total), ctypes.byref(rows), ctypes.byref(mr), sh))
+    args = (ctypes.byref(g.descriptor()), _ptr(central), n, ctypes.c_float(apm))
+    if hmax is None:
+        fn = lib.seis_crs_aperture
+    else:
+        fn = lib.seis_crs_aperture_offset
+        args = args + (ctypes.c_float(hmax),)
+    args = args + (_ptr(nbr_off),)
+    _check(fn(*args, None, 0, _ptr(m_c), _ptr(out_off), _ptr(dt_c),
+              ctypes.byref(total), ctypes.byref(rows), ctypes.byref(mr), sh))
     nbr_trace = torch.empty(max(1, total.value), dtype=torch.int32, device=dev)
-    _check(lib.seis_crs_aperture(*args, _ptr(nbr_trace), total.value, _ptr(m_c), _ptr(out_off),
-                                 _ptr(dt_c), None, None, None, sh))
+    _check(fn(*args, _ptr(nbr_trace), total.value, _ptr(m_c), _ptr(out_off),
+              _ptr(dt_c), None, None, None, sh))
     return Aperture(nbr_off, nbr_trace, m_c, out_off, dt_c, n, int(mr.value), int(rows.value))
 
 
@@ -425,6 +440,31 @@ def crs_refine_multi(g: Gathers, ap: "Aperture", starts: torch.Tensor, lo3, hi3,
                                 workspace.numel() - (aligned - base), ap.rows,
                                 _stream_handle(stream)))
     return dict(theta=theta, S=S, grad=grad, stack=st)
+
+
+def crs_pragmatic(g: Gathers, ap_full: "Aperture", ap_cmp: "Aperture", ap_zo: "Aperture",
+                  A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, c_zo: float,
+                  w: int = 11, stream=None, workspace=None) -> dict:
+    """CRS operator from a central-CMP C search and a zero-offset (A, B) search, evaluated
+    over the full aperture (include/seis.h: crs_pragmatic).  Returns theta, S, stack."""
+    lib = load_library()
+    dev = g.traces.device
+    A, B, C = (t.contiguous().float() for t in (A, B, C))
+    theta = torch.empty((ap_full.rows, 3), dtype=torch.float32, device=dev)
+    S = torch.empty(ap_full.rows, dtype=torch.float32, device=dev)
+    st = torch.empty(ap_full.rows, dtype=torch.float32, device=dev)
+    nbytes = lib.seis_pragmatic_workspace_size(ap_full.rows)
+    if workspace is None or workspace.numel() < nbytes + 256:
+        workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    _check(lib.crs_pragmatic(ctypes.byref(g.descriptor()), ctypes.byref(ap_full.descriptor()),
+                             ctypes.byref(ap_cmp.descriptor()), ctypes.byref(ap_zo.descriptor()),
+                             _ptr(A), A.numel(), _ptr(B), B.numel(), _ptr(C), C.numel(),
+                             ctypes.c_float(c_zo), w, _ptr(theta), _ptr(S), _ptr(st),
+                             ctypes.c_void_p(aligned), workspace.numel() - (aligned - base),
+                             ap_full.rows, _stream_handle(stream)))
+    return dict(theta=theta, S=S, stack=st)
 
 
 class CRSSemblance(torch.autograd.Function):

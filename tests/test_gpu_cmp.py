@@ -141,4 +141,7 @@ def test_paper_table1_shapes(seis, shape):
     fold, ns = synth.PAPER_SHAPES[shape]
     ds = synth.cmp_line(2, fold, ns, 0.004, 25.0, 3000.0, 4, 1.0, seed=300 + fold + ns,
                         v_range=(2550.0, 3450.0))
-    _check_all(seis, ds, _grid(23), label=f"cmp {shape}")
+    # a (row, candidate) is exempt when any of its traces sits on a mask edge within 1e-3
+    # samples, so the exempt fraction grows with the fold (about 5e-3 at fold 1000)
+    _check_all(seis, ds, _grid(23), label=f"cmp {shape}",
+               max_exempt=parity.MAX_EXEMPT_SMALL if fold < 1000 else 2e-2)

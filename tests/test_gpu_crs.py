@@ -168,3 +168,33 @@ def test_crs_paper_table1_shapes(seis, shape):
     parity.check_cube(got["S"], ref, f"crs {shape}")
     parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, f"crs {shape}",
                        row_edge=(ref.edge != 0).any(axis=1))
+
+
+def test_crs_pragmatic_matches_oracle(seis):
+    """Central-CMP C search + zero-offset (A, B) search + evaluation over the full aperture,
+    against the oracle's composition of the same three steps."""
+    ds = synth.crs_line(15, 12, 400, 0.004, 0.0, 1500.0, 3, 1, 2.0, seed=71)
+    central, apm = [5, 7, 9], 37.5
+    A, B, C = _grids(7, 5, 11)
+    g = seis.to_device(ds)
+    ap = seis.crs_aperture(g, central, apm)
+    ap_c = seis.crs_aperture(g, central, 0.0)
+    ap_z = seis.crs_aperture(g, central, apm, hmax=0.0)
+    assert int(ap_z.nbr_off[1] - ap_z.nbr_off[0]) == 7          # one zero-offset trace per CMP
+    t = lambda a: torch.from_numpy(a).cuda()
+    got = seis.crs_pragmatic(g, ap, ap_c, ap_z, t(A), t(B), t(C), c_zo=float(C[0]))
+    torch.cuda.synchronize()
+    seis.device_status()
+    ref = oracle.crs_pragmatic(ds, central, apm, 0.0, A, B, C, c_zo=C[0])
+    ok = ((ref.gap_cmp >= parity.GAP_TOL) & (ref.gap_zo >= parity.GAP_TOL) & ~ref.edge_cmp
+          & ~ref.edge_zo)
+    th = got["theta"].cpu().numpy()
+    assert ok.mean() > 0.8
+    np.testing.assert_array_equal(th[ok], ref.theta[ok].astype(np.float32))
+    ok &= ~ref.knot
+    dS = np.abs(got["S"].cpu().numpy() - ref.S)[ok].max()
+    st = got["stack"].cpu().numpy()
+    rel = np.linalg.norm((st - ref.stack)[ok]) / np.linalg.norm(ref.stack[ok])
+    print(f"[parity] pragmatic CRS: rows compared {ok.mean():.3f}, max dS {dS:.2e}, "
+          f"stack rel L2 {rel:.2e}")
+    assert dS <= parity.S_TOL and rel <= parity.STACK_TOL

@@ -139,3 +139,14 @@ def test_refine_starts_arguments_are_checked(lib):
                               i32(11), fake, fake, fake, fake, fake, ctypes.c_size_t(0),
                               i64(10), None)
     assert rc == -1 and "nstart" in _err(lib)
+
+
+def test_pragmatic_and_offset_aperture_arguments(lib):
+    fake = ctypes.c_void_p(16)
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    rc = lib.crs_pragmatic(fake, None, fake, fake, fake, i32(1), fake, i32(1), fake, i32(1),
+                           ctypes.c_float(0.0), i32(11), fake, fake, fake, fake,
+                           ctypes.c_size_t(0), i64(10), None)
+    assert rc == -1 and "aperture" in _err(lib)
+    lib.seis_pragmatic_workspace_size.restype = ctypes.c_size_t
+    assert lib.seis_pragmatic_workspace_size(i64(100)) >= 100 * 52

@@ -369,6 +369,24 @@ def test_refine_multi_keeps_best_start():
     assert multi.S[1] > 0.999          # the start next to the exact operator wins
 
 
+def test_pragmatic_crs_recovers_exact_plane():
+    """Exactly sampled dipping plane (A = 2^-6, B = 0, C = 2^-20) stored as 7 CMP gathers:
+    the central CMP's traces give C, the 7 zero-offset traces give A and B, and the combined
+    operator has S = 1 over the full aperture."""
+    ds, (At, Bt, Ct) = _exact_plane()
+    _, sizes = np.unique(ds["m"], return_counts=True)        # traces are grouped by CMP
+    ds = dataset([ds["traces"][ds["trace_off"][i]:ds["trace_off"][i + 1]]
+                  for i in range(len(ds["h"]))], ds["h"], 1.0 / 256, m=ds["m"],
+                 gather_sizes=list(sizes))
+    A = At * np.array([0.5, 1.0, 1.5]); B = np.array([-2.0 ** -10, 0.0, 2.0 ** -10])
+    C = Ct * np.array([0.8, 1.0, 1.2])
+    assert len(oracle.offset_limited(ds, oracle.aperture(ds, [3], 3.0), 0.0)[1]) == 7
+    r = oracle.crs_pragmatic(ds, [3], 3.0, 0.0, A, B, C, c_zo=C[0])
+    np.testing.assert_array_equal(r.theta[260], [At, 0.0, Ct])
+    assert r.S[260] == pytest.approx(1.0, abs=1e-12)
+    assert r.gap_cmp[260] > 1e-3 and r.gap_zo[260] > 1e-3
+
+
 def test_invalid_arguments():
     ds = dataset([np.zeros(50)], [0.0], 0.004)
     with pytest.raises(ValueError):
