@@ -534,6 +534,48 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
                         clk, launches)
 
 
+def run_t0win(args, torch, dist, seis, synth, rank, world, dev):
+    """The window over neighbouring output times (one interpolation per intersection)
+    against the paper's window along each trace, on the cmp-line workload."""
+    ds = synth.workload_cmp_line(seed=2 + 1000 * rank, G=args.gathers)
+    C = _candidates()
+    inter = _intersections(ds, NC)
+    g = seis.to_device(ds, dev)
+    Cd = torch.from_numpy(C).to(dev)
+    stream = torch.cuda.current_stream()
+    out_t = seis.cmp_semblance_t0win(g, Cd, w=W)
+    out_p = seis.cmp_semblance(g, Cd, w=W)
+    for _ in range(args.warmup):
+        seis.cmp_semblance_t0win(g, Cd, w=W, out=out_t)
+    torch.cuda.synchronize()
+    seis.device_status()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    kern, total = _time_steps(torch, stream, lambda: seis.cmp_semblance_t0win(g, Cd, w=W, out=out_t),
+                              args.steps)
+    clk = clocks.stop()
+    ms = total / args.steps
+    _, total_p = _time_steps(torch, stream, lambda: seis.cmp_semblance(g, Cd, w=W, out=out_p), 1)
+    seis.device_status()
+    same = (out_t["best_idx"] == out_p["best_idx"]).float().mean().item()
+    near = ((out_t["best_idx"] - out_p["best_idx"]).abs() <= 2).float().mean().item()
+    strong = out_p["best_S"] >= 0.1
+    same_strong = ((out_t["best_idx"] == out_p["best_idx"]) & strong).sum().item() / max(
+        1, strong.sum().item())
+    return _simple_line("CMP t0-window semblance intersections/s", inter * world / (ms / 1e3),
+                        ms, args, world,
+                        {"workload": f"cmp-line: {g.ngathers} gathers x fold 60 x 2000 samples "
+                                     "@4ms, 201 C, w=11; window over neighbouring output times "
+                                     "(one interpolated sample per intersection)",
+                         "intersections_per_step": inter * world},
+                        {"unit": "intersections/s",
+                         "paper_window_ms": total_p, "speedup_vs_paper_window": total_p / ms,
+                         "rows_same_pick_as_paper_window": same,
+                         "rows_pick_within_2_candidates": near,
+                         "rows_same_pick_where_paper_S_ge_0.1": same_strong},
+                        clk, args.steps)
+
+
 def run_pragmatic(args, torch, dist, seis, synth, rank, world, dev):
     """The CRS operator by a central-CMP C search and a zero-offset (A, B) search, against
     the dense 21 x 21 x 41 search on the same centrals (crs-line workload)."""
@@ -691,7 +733,8 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     seis_build.build()
     fn = {"cmp-line": run_cmp_line, "crs-line": run_crs_line, "batch": run_batch,
-          "refine": run_refine, "paper": run_paper, "pragmatic": run_pragmatic}[args.workload]
+          "refine": run_refine, "paper": run_paper, "pragmatic": run_pragmatic,
+          "t0win": run_t0win}[args.workload]
     line = fn(args, torch, dist, seis, synth, rank, world, dev)
     if world > 1:
         dist.barrier()
@@ -747,7 +790,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cmp-line",
-                    choices=["cmp-line", "crs-line", "batch", "refine", "paper", "pragmatic"])
+                    choices=["cmp-line", "crs-line", "batch", "refine", "paper", "pragmatic",
+                             "t0win"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)

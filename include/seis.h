@@ -144,6 +144,20 @@ int cmp_semblance(const seis_gathers* d, const float* C, int32_t nc, int32_t w,
                   float* S_cube, int32_t* best_idx, float* best_C, float* best_S,
                   float* stack_out, void* stream);
 
+/* CMP semblance with the window over neighbouring output times (not the paper's method:
+ * Algorithm 1 windows along each trace around its own intersection).  For output time
+ * t0 = n dt and candidate C, the window runs over t0' = t0 + j dt (j = -hw..hw, rows of
+ * the same gather only), each with its own traveltime t = sqrt(t0'^2 + C h^2) (Section
+ * 2.1), and every trace gives one linearly interpolated sample v there; a trace takes part
+ * at t0' when both interpolation samples lie inside it.  With s, e, M the sum of v, of v^2
+ * and the count of traces taking part at t0':
+ *   S = sum_j s(t0')^2 / sum_j M(t0') e(t0')   (0 if the denominator is 0),
+ * stack_out = s(t0) / M(t0) at the pick.  Arguments, layouts and errors as cmp_semblance
+ * (one launch; no workspace). */
+int cmp_semblance_t0win(const seis_gathers* d, const float* C, int32_t nc, int32_t w,
+                        float* S_cube, int32_t* best_idx, float* best_C, float* best_S,
+                        float* stack_out, void* stream);
+
 /* CRS aperture build -- Section 2.2 (the central CDP uses the traces of the CDPs within
  * radius r) and Section 3.5 (each CDP draws a circle around its midpoint).  For each
  * central gather central[c] (device int32 [n_central]) lists, in increasing order, every

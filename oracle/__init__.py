@@ -59,6 +59,7 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             lib.seis_oracle_cmp.restype = ctypes.c_int
+            lib.seis_oracle_cmp_t0win.restype = ctypes.c_int
             lib.seis_oracle_crs.restype = ctypes.c_int
             lib.seis_oracle_crs_eval.restype = ctypes.c_int
             lib.seis_oracle_crs_refine.restype = ctypes.c_int
@@ -100,11 +101,13 @@ class Result(dict):
     __getattr__ = dict.__getitem__
 
 
-def cmp_semblance(ds, C, w=11, rows=None, want_cube=True, knot_eps=1e-3, nthreads=0) -> Result:
+def cmp_semblance(ds, C, w=11, rows=None, want_cube=True, knot_eps=1e-3, nthreads=0,
+                  t0_window=False) -> Result:
     """CMP search (Eq. 1, Algorithm 1, Section 3.2) on dataset ``ds`` (dict of arrays:
     traces, trace_off, h, gather_off, out_off, dt).  ``rows``: global output rows to
     evaluate (default all).  Returns S [nrows, nc], N, edge, best_idx, best_S,
-    second_S, stack (FP64 / int)."""
+    second_S, stack (FP64 / int).  t0_window: the window over neighbouring output times
+    instead (reading c18, seis_oracle_cmp_t0win)."""
     lib = _load()
     traces = _c(ds["traces"], np.float32)
     trace_off = _c(ds["trace_off"], np.int64)
@@ -124,11 +127,12 @@ def cmp_semblance(ds, C, w=11, rows=None, want_cube=True, knot_eps=1e-3, nthread
     bs = np.empty(nrows, np.float64)
     b2 = np.empty(nrows, np.float64)
     st = np.empty(nrows, np.float64)
-    rc = lib.seis_oracle_cmp(_p(traces), _p(trace_off), _p(h), _p(gather_off), _p(out_off),
-                             _p(dt), ctypes.c_int64(G), _p(C), ctypes.c_int32(nc),
-                             ctypes.c_int32(w), _p(rows_a), ctypes.c_int64(nrows),
-                             _p(S), _p(N), _p(edge), _p(bi), _p(bs), _p(b2), _p(st),
-                             ctypes.c_double(knot_eps), ctypes.c_int32(nthreads))
+    fn = lib.seis_oracle_cmp_t0win if t0_window else lib.seis_oracle_cmp
+    rc = fn(_p(traces), _p(trace_off), _p(h), _p(gather_off), _p(out_off),
+            _p(dt), ctypes.c_int64(G), _p(C), ctypes.c_int32(nc),
+            ctypes.c_int32(w), _p(rows_a), ctypes.c_int64(nrows),
+            _p(S), _p(N), _p(edge), _p(bi), _p(bs), _p(b2), _p(st),
+            ctypes.c_double(knot_eps), ctypes.c_int32(nthreads))
     if rc != 0:
         raise ValueError("seis_oracle_cmp: invalid arguments")
     return Result(S=S, N=N, edge=edge, best_idx=bi, best_S=bs, second_S=b2, stack=st)

@@ -216,6 +216,88 @@ int seis_oracle_cmp(const float* traces, const int64_t* trace_off, const float* 
 }
 
 /* ------------------------------------------------------------------------- */
+/* t0-window CMP semblance (reading c18; not the paper's method, whose window runs along
+ * each trace around its own intersection, Algorithm 1).  The window runs over the
+ * neighbouring output times t0' = (n + j) dt, j = -hw..hw, of the same gather, each with
+ * its own traveltime (Section 2.1), and every trace gives one interpolated sample there:
+ *   u = sqrt(t0'^2 + C h^2) / dt, k = floor(u), x = u - k, v = f[k] + x (f[k+1] - f[k]);
+ *   the trace takes part at t0' iff k >= 0 and k + 1 <= ns - 1;
+ *   s(t0') = sum of v, e(t0') = sum of v^2, M(t0') = traces taking part;
+ *   S(t0) = sum_j s(t0')^2 / sum_j M(t0') e(t0')   (0 if that denominator is 0),
+ * where output times outside the gather's rows contribute nothing; the stack at the pick
+ * is s(t0) / M(t0) (0 if M(t0) = 0).  Same outputs as seis_oracle_cmp (Nvalid = M(t0)). */
+static int sample_inside(double u, int64_t ns)
+{
+    if (!(u == u)) return 0;
+    const double kf = floor(u);
+    return kf >= 0.0 && kf + 1.0 <= (double)(ns - 1);
+}
+
+int seis_oracle_cmp_t0win(const float* traces, const int64_t* trace_off, const float* h,
+                          const int64_t* gather_off, const int64_t* out_off, const float* dt,
+                          int64_t G, const float* C, int32_t nc, int32_t w,
+                          const int64_t* rows, int64_t nrows,
+                          double* S, int32_t* Nvalid, int8_t* edge,
+                          int32_t* best_idx, double* best_S, double* second_S, double* stack,
+                          double knot_eps, int32_t nthreads)
+{
+    if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || nc < 1 || G < 1) return -1;
+    const int hw = w / 2;
+    if (!rows) nrows = out_off[G];
+    set_threads(nthreads);
+
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t e = 0; e < nrows; ++e) {
+        const int64_t r = rows ? rows[e] : e;
+        const int64_t g = owner_of(out_off, G, r);
+        const int64_t n = r - out_off[g];
+        const int64_t nrow_g = out_off[g + 1] - out_off[g];
+        const double dtg = (double)dt[g];
+        int32_t bi = -1; double bs = -1.0, b2 = -1.0, bst = 0.0;
+        for (int32_t c = 0; c < nc; ++c) {
+            const double Cc = (double)C[c];
+            double num = 0.0, den = 0.0, s0 = 0.0; int64_t M0 = 0; int flag = 0;
+            for (int j = -hw; j <= hw; ++j) {
+                const int64_t n2 = n + j;
+                if (n2 < 0 || n2 >= nrow_g) continue;
+                const double t0 = (double)n2 * dtg;
+                double sj = 0.0, ej = 0.0; int64_t Mj = 0;
+                for (int64_t i = gather_off[g]; i < gather_off[g + 1]; ++i) {
+                    const double hi = (double)h[i];
+                    const int64_t ns_i = trace_off[i + 1] - trace_off[i];
+                    const double u = sqrt(t0 * t0 + Cc * hi * hi) / dtg;
+                    if (edge && !zero_moveout(0.0, 0.0, Cc, 0.0, hi) &&
+                        sample_inside(u - knot_eps, ns_i) != sample_inside(u + knot_eps, ns_i))
+                        flag = 1;
+                    if (!sample_inside(u, ns_i)) continue;
+                    const int64_t k = (int64_t)floor(u);
+                    const double x = u - (double)k;
+                    const float* f = traces + trace_off[i];
+                    const double v = ((double)f[k + 1] - (double)f[k]) * x + (double)f[k];
+                    sj += v;
+                    ej += v * v;
+                    ++Mj;
+                }
+                num += sj * sj;
+                den += (double)Mj * ej;
+                if (j == 0) { s0 = sj; M0 = Mj; }
+            }
+            const double sv = (den > 0.0) ? num / den : 0.0;
+            if (S) S[e * nc + c] = sv;
+            if (Nvalid) Nvalid[e * nc + c] = (int32_t)M0;
+            if (edge) edge[e * nc + c] = (int8_t)flag;
+            if (sv > bs) { b2 = bs; bs = sv; bi = c; bst = M0 ? s0 / (double)M0 : 0.0; }
+            else if (sv > b2) b2 = sv;
+        }
+        if (best_idx) best_idx[e] = bi;
+        if (best_S) best_S[e] = bs;
+        if (second_S) second_S[e] = b2;
+        if (stack) stack[e] = bst;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* CRS aperture (Section 2.2, Section 3.5): for each central gather, every trace whose
  * midpoint lies within the radius apm of the central CDP's midpoint (inclusive).  The
  * central midpoint is the midpoint of the central gather's first trace.  Traces are

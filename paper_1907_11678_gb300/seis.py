@@ -64,6 +64,7 @@ def load_library(path: str | None = None):
             lib.seis_last_error.restype = ctypes.c_char_p
             lib.seis_device_status.argtypes = [vp]
             lib.cmp_semblance.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+            lib.cmp_semblance_t0win.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
             lib.crs_semblance.argtypes = [vp, vp, vp, i32, vp, i32, vp, i32, i32,
                                           vp, vp, vp, vp, vp, vp]
             lib.seis_crs_aperture.argtypes = [vp, vp, i64, f32, vp, vp, i64, vp, vp, vp,
@@ -108,7 +109,7 @@ def load_library(path: str | None = None):
                          "seis_autotune_load", "seis_autotune_clear", "stack",
                          "crs_semblance_grad", "crs_refine", "crs_top_starts",
                          "crs_refine_multi", "seis_batch_semblance", "seis_autotune_batch",
-                         "seis_crs_aperture_offset", "crs_pragmatic",
+                         "seis_crs_aperture_offset", "crs_pragmatic", "cmp_semblance_t0win",
                          "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -208,6 +209,27 @@ def cmp_semblance(g: Gathers, C: torch.Tensor, w: int = 11, want_cube: bool = Fa
                            _ptr(out["best_idx"]), _ptr(out.get("best_C")), _ptr(out["best_S"]),
                            _ptr(out["stack"]), _stream_handle(stream))
     _check(rc)
+    return out
+
+
+def cmp_semblance_t0win(g: Gathers, C: torch.Tensor, w: int = 11, want_cube: bool = False,
+                        stream=None, out: dict | None = None) -> dict:
+    """CMP semblance with the window over neighbouring output times (include/seis.h:
+    cmp_semblance_t0win).  Same outputs as cmp_semblance."""
+    lib = load_library()
+    dev = g.traces.device
+    nc = int(C.numel())
+    if out is None:
+        out = dict(best_idx=torch.empty(g.rows, dtype=torch.int32, device=dev),
+                   best_C=torch.empty(g.rows, dtype=torch.float32, device=dev),
+                   best_S=torch.empty(g.rows, dtype=torch.float32, device=dev),
+                   stack=torch.empty(g.rows, dtype=torch.float32, device=dev))
+        if want_cube:
+            out["S"] = torch.empty((g.rows, nc), dtype=torch.float32, device=dev)
+    _check(lib.cmp_semblance_t0win(ctypes.byref(g.descriptor()), _ptr(C), nc, w,
+                                   _ptr(out.get("S")), _ptr(out["best_idx"]),
+                                   _ptr(out.get("best_C")), _ptr(out["best_S"]),
+                                   _ptr(out["stack"]), _stream_handle(stream)))
     return out
 
 

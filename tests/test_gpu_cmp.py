@@ -145,3 +145,47 @@ def test_paper_table1_shapes(seis, shape):
     # samples, so the exempt fraction grows with the fold (about 5e-3 at fold 1000)
     _check_all(seis, ds, _grid(23), label=f"cmp {shape}",
                max_exempt=parity.MAX_EXEMPT_SMALL if fold < 1000 else 2e-2)
+
+
+# --- t0-window semblance (window over neighbouring output times) -------------------------
+
+def _check_t0win(seis, ds, C, w, label, max_exempt=parity.MAX_EXEMPT_SMALL):
+    g = seis.to_device(ds)
+    out = seis.cmp_semblance_t0win(g, torch.from_numpy(C).cuda(), w=w, want_cube=True)
+    torch.cuda.synchronize()
+    seis.device_status()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    ref = oracle.cmp_semblance(ds, C, w=w, t0_window=True)
+    parity.check_cube(got["S"], ref, label, max_exempt=max_exempt)
+    rep = parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, label,
+                             row_edge=(ref.edge != 0).any(axis=1))
+    np.testing.assert_array_equal(got["best_C"], C[got["best_idx"]])
+    return rep
+
+
+@pytest.mark.parametrize("w", [1, 3, 11, 15])
+def test_t0win_windows_and_tiles(seis, w):
+    """Several windows: tiles of 32 - 2 hw output rows, halo lanes across tile edges."""
+    ds = synth.cmp_line(3, 13, 333, 0.004, 0.0, 1800.0, 3, 1.5, seed=420 + w)
+    _check_t0win(seis, ds, _grid(37), w, f"t0win w{w}")
+
+
+def test_t0win_ragged_traces(seis):
+    """Traces shorter and longer than the gather's output rows."""
+    rng = np.random.default_rng(411)
+    traces, h = [], []
+    for g in range(3):
+        for i in range(11):
+            traces.append(rng.normal(size=int(rng.integers(150, 260))))
+            h.append(150.0 * i)
+    ds = dataset(traces, h, 0.004, gather_sizes=[11] * 3, out_ns=[203, 257, 96])
+    _check_t0win(seis, ds, _grid(29), 11, "t0win ragged")
+
+
+def test_t0win_cmp_small_workload(seis):
+    ds = synth.workload_cmp_small()
+    # an entry is exempt when any trace at any of the w output times of its window sits on
+    # a mask edge, so about w times as many entries are exempt as for the paper's window
+    rep = _check_t0win(seis, ds, _grid(101), 11, "t0win cmp-small",
+                       max_exempt=11 * parity.MAX_EXEMPT)
+    assert rep["pick_agree"] > 0.99

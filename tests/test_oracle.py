@@ -3,6 +3,8 @@ the oracle itself (CPU only)."""
 import json
 import os
 
+import math
+
 import numpy as np
 import pytest
 
@@ -385,6 +387,78 @@ def test_pragmatic_crs_recovers_exact_plane():
     np.testing.assert_array_equal(r.theta[260], [At, 0.0, Ct])
     assert r.S[260] == pytest.approx(1.0, abs=1e-12)
     assert r.gap_cmp[260] > 1e-3 and r.gap_zo[260] > 1e-3
+
+
+# --- t0-window semblance (reading c18) --------------------------------------------------
+
+def _t0win_brute(ds, C, w, g, n):
+    """The reading c18 definition written out in plain Python for one (gather, row)."""
+    hw = w // 2
+    t0s = [(n + j) for j in range(-hw, hw + 1)]
+    nrow = int(ds["out_off"][g + 1] - ds["out_off"][g])
+    dt = float(ds["dt"][g])
+    out = []
+    for Cc in C:
+        num = den = 0.0
+        for n2 in t0s:
+            if n2 < 0 or n2 >= nrow:
+                continue
+            s = e = 0.0
+            M = 0
+            for i in range(int(ds["gather_off"][g]), int(ds["gather_off"][g + 1])):
+                f = ds["traces"][ds["trace_off"][i]:ds["trace_off"][i + 1]]
+                u = math.sqrt((n2 * dt) ** 2 + float(Cc) * float(ds["h"][i]) ** 2) / dt
+                k = math.floor(u)
+                if k < 0 or k + 1 > len(f) - 1:
+                    continue
+                v = float(f[k]) + (u - k) * (float(f[k + 1]) - float(f[k]))
+                s += v
+                e += v * v
+                M += 1
+            num += s * s
+            den += M * e
+        out.append(num / den if den > 0 else 0.0)
+    return np.array(out)
+
+
+def test_t0win_brute_force_tiny():
+    rng = np.random.default_rng(21)
+    traces = [rng.normal(size=40) for _ in range(5)]
+    ds = dataset(traces, [0.0, 10.0, 35.0, 60.0, 90.0], 0.004, gather_sizes=[3, 2])
+    C = np.float32([0.0, 3e-7, 1.2e-6, 4e-6])
+    r = oracle.cmp_semblance(ds, C, w=5, t0_window=True)
+    for row in (0, 1, 7, 20, 38, 39, 40, 45, 79):
+        g = 0 if row < 40 else 1
+        np.testing.assert_allclose(r.S[row], _t0win_brute(ds, C, 5, g, row - 40 * g),
+                                   rtol=1e-12, atol=1e-15)
+
+
+def test_t0win_equals_paper_window_at_zero_moveout():
+    """At C = 0 every traveltime is the output time itself (x = 0), so on rows whose whole
+    window lies inside every trace the two windows read the same samples: equal S."""
+    rng = np.random.default_rng(22)
+    ds = dataset([rng.normal(size=120) for _ in range(6)], np.linspace(0, 500, 6), 0.004)
+    a = oracle.cmp_semblance(ds, [0.0], w=7)
+    b = oracle.cmp_semblance(ds, [0.0], w=7, t0_window=True)
+    rows = np.arange(3, 116)                  # k - 3 >= 0 and k + 4 <= 119
+    np.testing.assert_allclose(b.S[rows, 0], a.S[rows, 0], rtol=1e-12, atol=1e-15)
+
+
+def test_t0win_invariants():
+    rng = np.random.default_rng(23)
+    C = np.float32(np.linspace(0, 2e-6, 9))
+    ds = dataset([np.full(200, 1.7) for _ in range(4)], [0, 100, 300, 700], 0.004)
+    r = oracle.cmp_semblance(ds, C, w=11, t0_window=True)
+    live = r.N > 0
+    np.testing.assert_allclose(r.S[live], 1.0, rtol=0, atol=1e-14)     # constant traces
+    one = dataset([rng.normal(size=150)], [250.0], 0.004)
+    r1 = oracle.cmp_semblance(one, C, w=9, t0_window=True)
+    np.testing.assert_allclose(r1.S[r1.N > 0], 1.0, rtol=0, atol=1e-14)  # a single trace
+    noisy = dataset([rng.normal(size=300) for _ in range(8)], np.linspace(0, 1400, 8), 0.004)
+    r2 = oracle.cmp_semblance(noisy, C, w=11, t0_window=True)
+    assert np.all(r2.S >= 0) and np.all(r2.S <= 1 + 1e-12)              # Cauchy-Schwarz
+    zero = dataset([np.zeros(100) for _ in range(3)], [0, 50, 90], 0.004)
+    assert np.all(oracle.cmp_semblance(zero, C, t0_window=True).S == 0)
 
 
 def test_invalid_arguments():
