@@ -543,6 +543,10 @@ def run_t0win(args, torch, dist, seis, synth, rank, world, dev):
     g = seis.to_device(ds, dev)
     Cd = torch.from_numpy(C).to(dev)
     stream = torch.cuda.current_stream()
+    # the paper's window runs with the variant the autotuner picks for this shape
+    sub = synth.cmp_line(min(512, args.gathers), 60, 2000, 0.004, 25.0, 3000.0, 8, 1.0,
+                         seed=99, v_range=(2550.0, 3450.0), v_gradient=0.5)
+    seis.autotune_cmp(seis.to_device(sub, dev), Cd, w=W, reps=1)
     out_t = seis.cmp_semblance_t0win(g, Cd, w=W)
     out_p = seis.cmp_semblance(g, Cd, w=W)
     for _ in range(args.warmup):
@@ -555,7 +559,8 @@ def run_t0win(args, torch, dist, seis, synth, rank, world, dev):
                               args.steps)
     clk = clocks.stop()
     ms = total / args.steps
-    _, total_p = _time_steps(torch, stream, lambda: seis.cmp_semblance(g, Cd, w=W, out=out_p), 1)
+    _, total_p = _time_steps(torch, stream, lambda: seis.cmp_semblance(g, Cd, w=W, out=out_p), 2)
+    total_p /= 2
     seis.device_status()
     same = (out_t["best_idx"] == out_p["best_idx"]).float().mean().item()
     near = ((out_t["best_idx"] - out_p["best_idx"]).abs() <= 2).float().mean().item()

@@ -18,9 +18,11 @@ namespace seis {
 
 namespace {
 
-constexpr int kTwWarps = 15;          // consumer warps
-constexpr int kTwR = 2;               // candidates per thread
+constexpr int kTwWarps = 13;          // consumer warps
+constexpr int kTwR = 4;               // candidates per thread (independent traveltime chains)
 constexpr int kTwCB = kTwWarps * kTwR;
+static_assert(kTwCB <= 64, "the producer bounds two candidates per lane");
+static_assert(kTwWarps <= kMaxWarps, "reduction arrays are sized for kMaxWarps");
 constexpr int kTwThreads = 32 * (kTwWarps + 1);
 
 struct TwAccum {
@@ -30,27 +32,43 @@ struct TwAccum {
     int cidx[kTwR];
 };
 
-// One interpolated sample per (row, candidate, trace) of a run of traces [t0, t1).
+// One interpolated sample per (row, candidate, trace) of a run of traces [t0, t1).  The
+// traveltimes of trace t+1 (the MUFU chains) are formed while trace t is interpolated.
 template <bool FAST>
 __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0, int t1,
                                        int slot_base, const RowConst& rc, int zidx,
                                        const float* smf) {
-    for (int t = t0; t < t1; ++t) {
+    int sI[kTwR];
+    float sX[kTwR];
+    bool sO[kTwR];
+    auto setup = [&](int t) {
         const TraceConst tc = trace_const(meta[t], rc.n, slot_base, 0);
         #pragma unroll
         for (int r = 0; r < kTwR; ++r) {
-            int idx;
-            float x;
             if constexpr (FAST) {
-                intersect_one_fast<false>(0.f, 0.f, a.Cr[r], tc, rc.nf, rc.nsq, idx, x);
-                a.M[r] += 1;
+                intersect_one_fast<false>(0.f, 0.f, a.Cr[r], tc, rc.nf, rc.nsq, sI[r], sX[r]);
+                sO[r] = true;
             } else {
-                bool ok;
-                intersect_one<false>(0.f, 0.f, a.Cr[r], tc, rc.nf, rc.nsq, zidx, idx, x, ok);
-                a.M[r] += ok ? 1 : 0;
+                intersect_one<false>(0.f, 0.f, a.Cr[r], tc, rc.nf, rc.nsq, zidx, sI[r], sX[r],
+                                     sO[r]);
             }
-            const float f0 = smf[idx], f1 = smf[idx + 1];
-            const float v = fmaf(x, f1 - f0, f0);
+        }
+    };
+    setup(t0);
+    for (int t = t0; t < t1; ++t) {
+        int cI[kTwR];
+        float cX[kTwR];
+        #pragma unroll
+        for (int r = 0; r < kTwR; ++r) {
+            cI[r] = sI[r];
+            cX[r] = sX[r];
+            a.M[r] += sO[r] ? 1 : 0;
+        }
+        setup(min(t + 1, t1 - 1));
+        #pragma unroll
+        for (int r = 0; r < kTwR; ++r) {
+            const float f0 = smf[cI[r]], f1 = smf[cI[r] + 1];
+            const float v = fmaf(cX[r], f1 - f0, f0);
             a.s[r] += v;
             a.e[r] = fmaf(v, v, a.e[r]);
         }
@@ -129,12 +147,20 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
                 mbar_arrive(&sm.full[slot]);
                 break;
             }
-            if (pl_bpass != pl_pass) {
-                const int c = pl_pass * kTwCB + lane;
-                const bool v = lane < kTwCB && c < P.ncand;
-                const float cc = v ? P.C[c] : 0.f;
-                bC0 = warp_min(v ? cc : FLT_MAX);
-                bC1 = warp_max(v ? cc : -FLT_MAX);
+            if (pl_bpass != pl_pass) {   // C bounds of the pass, up to 64 candidates
+                float lo = FLT_MAX, hi = -FLT_MAX;
+                #pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int cl = lane + 32 * k;
+                    const int c = pl_pass * kTwCB + cl;
+                    if (cl < kTwCB && c < P.ncand) {
+                        const float cc = P.C[c];
+                        lo = fminf(lo, cc);
+                        hi = fmaxf(hi, cc);
+                    }
+                }
+                bC0 = warp_min(lo);
+                bC1 = warp_max(hi);
                 pl_bpass = pl_pass;
             }
             const int first = (pl_t == 0);
