@@ -422,7 +422,7 @@ __device__ __forceinline__ void intersect_one_fast(float A, float B, float C, co
 template <bool CRS>
 __device__ __forceinline__ void intersect_pair_fast(f2_t A2, f2_t B2, f2_t C2, const TraceConst& tc,
                                                     f2_t nf2, f2_t nsq2, int& ia, int& ib,
-                                                    float& xa, float& xb) {
+                                                    f2_t& x2) {
     const f2_t q2 = pk2(tc.q, tc.q);
     f2_t D2;
     if (CRS) {
@@ -448,10 +448,9 @@ __device__ __forceinline__ void intersect_pair_fast(f2_t A2, f2_t B2, f2_t C2, c
     }
     const f2_t shift2 = pk2(kFloorShift, kFloorShift);
     const f2_t t2 = add2_rm(D2, shift2);
-    const f2_t x2 = sub2(D2, sub2(t2, shift2));
+    x2 = sub2(D2, sub2(t2, shift2));                // fraction pair, kept packed
     float ta, tb;
     up2(t2, ta, tb);
-    up2(x2, xa, xb);
     ia = tc.kbase + (int)min((unsigned)(__float_as_int(ta) + tc.off), tc.rng);
     ib = tc.kbase + (int)min((unsigned)(__float_as_int(tb) + tc.off), tc.rng);
 }
@@ -533,6 +532,9 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
     int sI[kR];
     float sX[kR];
     bool sO[kR];
+    // check-free packed runs keep each pair's fractions as one f32x2 value
+    constexpr bool kX2 = FAST && CFG::kMode == kPacked;
+    f2_t sX2[kX2 ? kG : 1];
     auto setup = [&](int t) {
         const TraceConst tc = trace_const(meta[t], rc.n, slot_base, HW);
         if constexpr (CFG::kMode == kPacked) {
@@ -540,7 +542,7 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
             for (int g = 0; g < kG; ++g) {
                 if constexpr (FAST)
                     intersect_pair_fast<CRS>(a.A2[g], a.B2[g], a.C2[g], tc, rc.nf2, rc.nsq2,
-                                             sI[2 * g], sI[2 * g + 1], sX[2 * g], sX[2 * g + 1]);
+                                             sI[2 * g], sI[2 * g + 1], sX2[g]);
                 else
                     intersect_pair<CRS>(a.A2[g], a.B2[g], a.C2[g], tc, rc.nf2, rc.nsq2, zidx,
                                         sI[2 * g], sI[2 * g + 1], sX[2 * g], sX[2 * g + 1],
@@ -562,11 +564,16 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
     for (int t = t0; t < t1; ++t) {
         int cI[kR];
         float cX[kR];
+        f2_t cX2[kX2 ? kG : 1];
         #pragma unroll
         for (int r = 0; r < kR; ++r) {
             cI[r] = sI[r];
-            cX[r] = sX[r];
+            if constexpr (!kX2) cX[r] = sX[r];
             if constexpr (!FAST) a.cntv[r] += sO[r] ? 1 : 0;
+        }
+        if constexpr (kX2) {
+            #pragma unroll
+            for (int g = 0; g < kG; ++g) cX2[g] = sX2[g];
         }
         setup(min(t + 1, t1 - 1));
         #pragma unroll
@@ -586,7 +593,9 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
                 float FA[W + 1], FB[W + 1];
                 #pragma unroll
                 for (int j = 0; j <= W; ++j) { FA[j] = smf[cI[ra] + j]; FB[j] = smf[cI[rb] + j]; }
-                const f2_t x2 = pk2(cX[ra], cX[rb]);
+                f2_t x2;
+                if constexpr (kX2) x2 = cX2[g];
+                else x2 = pk2(cX[ra], cX[rb]);
                 #pragma unroll
                 for (int j = 0; j < W; ++j) {
                     f2_t v;
