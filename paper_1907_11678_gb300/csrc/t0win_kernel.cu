@@ -9,92 +9,147 @@
 //   stack(t0) = s(t0) / M(t0) at the pick.
 //
 // Same CTA structure as the search kernel (producer warp staging trace windows through the
-// shared-memory ring, consumer warps = candidates, lanes = rows), with lane l holding the
-// output time n0 - hw + l: the 32 lanes compute s, e, M for 32 consecutive rows and the
-// 32 - 2 hw middle lanes form the window sums of their neighbours by warp shuffles.
+// shared-memory ring, consumer warps = candidates, lanes = rows), with a block of 64
+// consecutive output times per CTA: lane l holds positions l and l + 32 as one f32x2 pair
+// (the traveltime and interpolation of both run in packed FP32), the 64 - 2 hw middle
+// positions are output rows, and each forms the window sums of its neighbours by warp
+// shuffles.
 #include "search_kernel.cuh"
 
 namespace seis {
 
 namespace {
 
-constexpr int kTwWarps = 13;          // consumer warps
-constexpr int kTwR = 4;               // candidates per thread (independent traveltime chains)
+constexpr int kTwWarps = 15;          // consumer warps
+constexpr int kTwR = 2;               // candidates per thread
 constexpr int kTwCB = kTwWarps * kTwR;
-static_assert(kTwCB <= 64, "the producer bounds two candidates per lane");
+static_assert(kTwCB <= 32, "the producer bounds one candidate per lane");
 static_assert(kTwWarps <= kMaxWarps, "reduction arrays are sized for kMaxWarps");
 constexpr int kTwThreads = 32 * (kTwWarps + 1);
 
+// Per thread: kTwR candidates at the lane's two output times (f32x2: .lo = row p0,
+// .hi = row p0 + 32).
 struct TwAccum {
-    float s[kTwR], e[kTwR];
-    int M[kTwR];
-    float Cr[kTwR];
+    f2_t s2[kTwR], e2[kTwR];
+    int M0[kTwR], M1[kTwR];
+    f2_t C2[kTwR];
     int cidx[kTwR];
 };
 
-// One interpolated sample per (row, candidate, trace) of a run of traces [t0, t1).  The
-// traveltimes of trace t+1 (the MUFU chains) are formed while trace t is interpolated.
+struct TwRows {
+    f2_t nf2, nsq2;      // (n0, n1) and their squares; inactive rows carry 2^24
+    int n0, n1;
+};
+
+// One interpolated sample per (row pair, candidate, trace) of a run of traces [t0, t1):
+// the traveltime pair D = Cq / (sqrt(n^2 + Cq) + n) in f32x2, floor and fraction by the
+// rounding shift, then v = f[k] + x (f[k+1] - f[k]).  The traveltimes of trace t+1 are
+// formed while trace t is interpolated.
 template <bool FAST>
 __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0, int t1,
-                                       int slot_base, const RowConst& rc, int zidx,
+                                       int slot_base, const TwRows& rw, int zidx,
                                        const float* smf) {
-    int sI[kTwR];
-    float sX[kTwR];
-    bool sO[kTwR];
+    int sI0[kTwR], sI1[kTwR];
+    f2_t sX2[kTwR];
+    bool sO0[kTwR], sO1[kTwR];
+    const f2_t shift2 = pk2(kFloorShift, kFloorShift);
     auto setup = [&](int t) {
-        const TraceConst tc = trace_const(meta[t], rc.n, slot_base, 0);
+        const TraceMeta& tm = meta[t];
+        const f2_t q2 = pk2(tm.q, tm.q);
+        const unsigned rng = (unsigned)(tm.kmax - tm.kmin);
+        const int kbase = slot_base + tm.base + tm.kmin;
+        const int off0 = rw.n0 - kFloorShiftBits - tm.kmin;
+        const int off1 = rw.n1 - kFloorShiftBits - tm.kmin;
         #pragma unroll
         for (int r = 0; r < kTwR; ++r) {
+            const f2_t cq2 = mul2(a.C2[r], q2);
+            const f2_t rad2 = add2(rw.nsq2, cq2);
+            float ra, rb;
+            up2(rad2, ra, rb);
+            const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), rw.nf2);
+            float sa, sb;
+            up2(sum2, sa, sb);
+            const f2_t D2 = mul2(cq2, pk2(rcp_fast(sa), rcp_fast(sb)));
+            const f2_t tt2 = add2_rm(D2, shift2);
+            f2_t x2 = sub2(D2, sub2(tt2, shift2));
+            float ta, tb;
+            up2(tt2, ta, tb);
+            const int kk0 = __float_as_int(ta) + off0;
+            const int kk1 = __float_as_int(tb) + off1;
             if constexpr (FAST) {
-                intersect_one_fast<false>(0.f, 0.f, a.Cr[r], tc, rc.nf, rc.nsq, sI[r], sX[r]);
-                sO[r] = true;
+                sI0[r] = kbase + (int)min((unsigned)kk0, rng);
+                sI1[r] = kbase + (int)min((unsigned)kk1, rng);
+                sO0[r] = sO1[r] = true;
             } else {
-                intersect_one<false>(0.f, 0.f, a.Cr[r], tc, rc.nf, rc.nsq, zidx, sI[r], sX[r],
-                                     sO[r]);
+                const bool ok0 = (unsigned)kk0 <= rng, ok1 = (unsigned)kk1 <= rng;
+                float xa, xb;
+                up2(x2, xa, xb);
+                x2 = pk2(ok0 ? xa : 0.f, ok1 ? xb : 0.f);   // a NaN fraction must not reach the sums
+                sI0[r] = ok0 ? kbase + kk0 : zidx;
+                sI1[r] = ok1 ? kbase + kk1 : zidx;
+                sO0[r] = ok0;
+                sO1[r] = ok1;
             }
+            sX2[r] = x2;
         }
     };
     setup(t0);
     for (int t = t0; t < t1; ++t) {
-        int cI[kTwR];
-        float cX[kTwR];
+        int cI0[kTwR], cI1[kTwR];
+        f2_t cX2[kTwR];
         #pragma unroll
         for (int r = 0; r < kTwR; ++r) {
-            cI[r] = sI[r];
-            cX[r] = sX[r];
-            a.M[r] += sO[r] ? 1 : 0;
+            cI0[r] = sI0[r];
+            cI1[r] = sI1[r];
+            cX2[r] = sX2[r];
+            a.M0[r] += sO0[r] ? 1 : 0;
+            a.M1[r] += sO1[r] ? 1 : 0;
         }
         setup(min(t + 1, t1 - 1));
         #pragma unroll
         for (int r = 0; r < kTwR; ++r) {
-            const float f0 = smf[cI[r]], f1 = smf[cI[r] + 1];
-            const float v = fmaf(cX[r], f1 - f0, f0);
-            a.s[r] += v;
-            a.e[r] = fmaf(v, v, a.e[r]);
+            const f2_t f0 = pk2(smf[cI0[r]], smf[cI1[r]]);
+            const f2_t f1 = pk2(smf[cI0[r] + 1], smf[cI1[r] + 1]);
+            const f2_t v2 = fma2(cX2[r], sub2(f1, f0), f0);
+            a.s2[r] = add2(a.s2[r], v2);
+            a.e2[r] = fma2(v2, v2, a.e2[r]);
         }
     }
 }
 
-// Sum over the lanes l + j, j = -hw..hw, that exist (lanes outside the warp give 0).
+// Window sums of the output time at position p = lane + 32 h (h = 0, 1) of the 64-row
+// block: positions p + j, j = -hw..hw, inside [0, 64).  Position q < 32 is lane q's .lo
+// value, q >= 32 is lane q - 32's .hi value.
 template <int HW>
-__device__ __forceinline__ void window_sums(float s, float me, int lane, float& num, float& den) {
-    num = 0.f;
-    den = 0.f;
+__device__ __forceinline__ void window_sums2(float s_lo, float s_hi, float m_lo, float m_hi,
+                                             int lane, float& num0, float& den0, float& num1,
+                                             float& den1) {
+    num0 = den0 = num1 = den1 = 0.f;
     #pragma unroll
     for (int j = -HW; j <= HW; ++j) {
-        const int src = lane + j;
-        const float sj = __shfl_sync(kFull, s, src & 31);
-        const float mj = __shfl_sync(kFull, me, src & 31);
-        const bool in = src >= 0 && src < 32;
-        num = in ? fmaf(sj, sj, num) : num;
-        den = in ? den + mj : den;
+        const int src = (lane + j) & 31;
+        const float sa = __shfl_sync(kFull, s_lo, src), sb = __shfl_sync(kFull, s_hi, src);
+        const float ma = __shfl_sync(kFull, m_lo, src), mb = __shfl_sync(kFull, m_hi, src);
+        const int q = lane + j;                     // position of row 0's neighbour
+        // row 0 (position lane): q < 0 outside, q < 32 a lo value, else a hi value
+        if (q >= 0) {
+            const float sv = q < 32 ? sa : sb, mv = q < 32 ? ma : mb;
+            num0 = fmaf(sv, sv, num0);
+            den0 += mv;
+        }
+        // row 1 (position 32 + lane): q < 0 a lo value, q < 32 a hi value, else outside
+        if (q < 32) {
+            const float sv = q < 0 ? sa : sb, mv = q < 0 ? ma : mb;
+            num1 = fmaf(sv, sv, num1);
+            den1 += mv;
+        }
     }
 }
 
 template <int W>
 __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams P) {
     constexpr int HW = W / 2;
-    constexpr int kT = 32 - 2 * HW;              // output rows per CTA
+    constexpr int kT = 64 - 2 * HW;              // output rows per CTA
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SearchSmem& sm = *reinterpret_cast<SearchSmem*>(smem_raw);
 
@@ -105,9 +160,9 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
     if (owner >= P.nowner) return;
     const int64_t row0 = P.out_off[owner];
     const int nrows = (int)(P.out_off[owner + 1] - row0);
-    const int out0 = tile * kT;                   // first output row of the CTA
-    if (out0 >= nrows) return;                    // whole CTA: uniform
-    const int lane_row0 = out0 - HW;              // row of lane 0
+    const int first_out = tile * kT;              // first output row of the CTA
+    if (first_out >= nrows) return;               // whole CTA: uniform
+    const int base = first_out - HW;              // row of position 0
     const int64_t lbeg = P.list_off[owner];
     const int64_t M64 = P.list_off[owner + 1] - lbeg;
     const int M = M64 < 0 ? 0 : (M64 > INT_MAX ? INT_MAX : (int)M64);
@@ -127,8 +182,8 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
 
     if (warp == kTwWarps) {
         // =============================== producer warp ================================
-        const int n_first = max(lane_row0, 0);
-        const int n_last = min(lane_row0 + 31, nrows - 1);
+        const int n_first = max(base, 0);
+        const int n_last = min(base + 63, nrows - 1);
         int pl_pass = 0, pl_t = 0, pl_bpass = -1;
         float bC0 = 0.f, bC1 = 0.f;
         int s = 0;
@@ -147,20 +202,12 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
                 mbar_arrive(&sm.full[slot]);
                 break;
             }
-            if (pl_bpass != pl_pass) {   // C bounds of the pass, up to 64 candidates
-                float lo = FLT_MAX, hi = -FLT_MAX;
-                #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int cl = lane + 32 * k;
-                    const int c = pl_pass * kTwCB + cl;
-                    if (cl < kTwCB && c < P.ncand) {
-                        const float cc = P.C[c];
-                        lo = fminf(lo, cc);
-                        hi = fmaxf(hi, cc);
-                    }
-                }
-                bC0 = warp_min(lo);
-                bC1 = warp_max(hi);
+            if (pl_bpass != pl_pass) {   // C bounds of the pass (one candidate per lane)
+                const int c = pl_pass * kTwCB + lane;
+                const bool v = lane < kTwCB && c < P.ncand;
+                const float cc = v ? P.C[c] : 0.f;
+                bC0 = warp_min(v ? cc : FLT_MAX);
+                bC1 = warp_max(v ? cc : -FLT_MAX);
                 pl_bpass = pl_pass;
             }
             const int first = (pl_t == 0);
@@ -186,15 +233,23 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
     // ================================ consumer warps =====================================
     const float* smf = reinterpret_cast<const float*>(smem_raw);
     const int zidx = (int)(reinterpret_cast<const float*>(sm.zeros) - smf);
-    const int n = lane_row0 + lane;
-    const bool act = n >= 0 && n < nrows;
-    const bool out = act && lane >= HW && lane < HW + kT;
-    const RowConst rc = row_const(act, n);
+    const int n0 = base + lane, n1 = base + 32 + lane;
+    const bool act0 = n0 >= 0 && n0 < nrows, act1 = n1 < nrows;
+    const bool is_out0 = act0 && lane >= HW;              // positions HW .. 63 - HW
+    const bool is_out1 = act1 && 32 + lane < 64 - HW;
+    TwRows rw;
+    rw.n0 = act0 ? n0 : (1 << 24);
+    rw.n1 = act1 ? n1 : (1 << 24);
+    {
+        const float f0 = fmaxf((float)rw.n0, 1e-30f), f1 = fmaxf((float)rw.n1, 1e-30f);
+        rw.nf2 = pk2(f0, f1);
+        rw.nsq2 = pk2(f0 * f0, f1 * f1);
+    }
     TwAccum a;
     #pragma unroll
     for (int r = 0; r < kTwR; ++r) a.cidx[r] = INT_MAX;
-    float bestS = -1.f, bestT = 0.f;
-    int bestC = INT_MAX;
+    float bestS0 = -1.f, bestT0 = 0.f, bestS1 = -1.f, bestT1 = 0.f;
+    int bestC0 = INT_MAX, bestC1 = INT_MAX;
     bool aborted = false;
 
     for (int s = 0;; ++s) {
@@ -214,11 +269,12 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
             #pragma unroll
             for (int r = 0; r < kTwR; ++r) {
                 const int c = d.pass * kTwCB + warp * kTwR + r;
+                const float cc = c < P.ncand ? P.C[c] : 0.f;
                 a.cidx[r] = c;
-                a.Cr[r] = c < P.ncand ? P.C[c] : 0.f;
-                a.s[r] = 0.f;
-                a.e[r] = 0.f;
-                a.M[r] = 0;
+                a.C2[r] = pk2(cc, cc);
+                a.s2[r] = 0ull;
+                a.e2[r] = 0ull;
+                a.M0[r] = a.M1[r] = 0;
             }
         }
         const int ntr = min(d.ntr, kChunkT);
@@ -230,8 +286,8 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
                 const unsigned rest = (fast ? ~d.allv : d.allv) >> t;
                 const int len = rest ? __ffs(rest) - 1 : 32;
                 const int t1 = min(ntr, t + len);
-                if (fast) tw_run<true>(a, sm.meta[slot], t, t1, slot_base, rc, zidx, smf);
-                else tw_run<false>(a, sm.meta[slot], t, t1, slot_base, rc, zidx, smf);
+                if (fast) tw_run<true>(a, sm.meta[slot], t, t1, slot_base, rw, zidx, smf);
+                else tw_run<false>(a, sm.meta[slot], t, t1, slot_base, rw, zidx, smf);
                 t = t1;
             }
         }
@@ -239,35 +295,52 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
             #pragma unroll
             for (int r = 0; r < kTwR; ++r) {
                 const int c = a.cidx[r];
-                // inactive rows contributed nothing, so their s, e, M are 0
-                const float sr = act ? a.s[r] : 0.f;
-                const float me = act ? (float)a.M[r] * a.e[r] : 0.f;
-                float num, den;
-                window_sums<HW>(sr, me, lane, num, den);
-                if (c >= P.ncand || !out) continue;
-                const float sv = den > 0.f ? num / den : 0.f;
-                const float st = a.M[r] > 0 ? a.s[r] / (float)a.M[r] : 0.f;
-                if (P.S_cube) P.S_cube[(row0 + n) * (int64_t)P.ncand + c] = sv;
-                if (sv > bestS) { bestS = sv; bestC = c; bestT = st; }
+                float s_lo, s_hi, e_lo, e_hi;
+                up2(a.s2[r], s_lo, s_hi);
+                up2(a.e2[r], e_lo, e_hi);
+                // inactive rows contributed nothing: their s, e, M count as 0
+                if (!act0) { s_lo = 0.f; e_lo = 0.f; }
+                if (!act1) { s_hi = 0.f; e_hi = 0.f; }
+                const float m_lo = act0 ? (float)a.M0[r] * e_lo : 0.f;
+                const float m_hi = act1 ? (float)a.M1[r] * e_hi : 0.f;
+                float num0, den0, num1, den1;
+                window_sums2<HW>(s_lo, s_hi, m_lo, m_hi, lane, num0, den0, num1, den1);
+                if (c >= P.ncand) continue;
+                if (is_out0) {
+                    const float sv = den0 > 0.f ? num0 / den0 : 0.f;
+                    const float st = a.M0[r] > 0 ? s_lo / (float)a.M0[r] : 0.f;
+                    if (P.S_cube) P.S_cube[(row0 + n0) * (int64_t)P.ncand + c] = sv;
+                    if (sv > bestS0) { bestS0 = sv; bestC0 = c; bestT0 = st; }
+                }
+                if (is_out1) {
+                    const float sv = den1 > 0.f ? num1 / den1 : 0.f;
+                    const float st = a.M1[r] > 0 ? s_hi / (float)a.M1[r] : 0.f;
+                    if (P.S_cube) P.S_cube[(row0 + n1) * (int64_t)P.ncand + c] = sv;
+                    if (sv > bestS1) { bestS1 = sv; bestC1 = c; bestT1 = st; }
+                }
             }
         }
         mbar_arrive(&sm.empty[slot]);
     }
 
-    sm.redS[warp][lane] = bestS;
-    sm.redC[warp][lane] = bestC;
-    sm.redT[warp][lane] = bestT;
-    consumer_bar(32 * kTwWarps);
-    if (aborted || sm.abort_flag) return;
-    if (warp == 0 && out) {
-        float bs, bt;
-        int bc;
-        reduce_best(sm, kTwWarps, lane, bs, bc, bt);
-        const int64_t row = row0 + n;
-        P.best_idx[row] = bc;
-        P.best_S[row] = bs;
-        P.stack[row] = bt;
-        if (P.best_param) P.best_param[row] = P.C[bc];
+    // two rounds of the cross-warp argmax: the lane's lower row, then its upper row
+    for (int h = 0; h < 2; ++h) {
+        sm.redS[warp][lane] = h ? bestS1 : bestS0;
+        sm.redC[warp][lane] = h ? bestC1 : bestC0;
+        sm.redT[warp][lane] = h ? bestT1 : bestT0;
+        consumer_bar(32 * kTwWarps);
+        const bool outh = h ? is_out1 : is_out0;
+        if (!aborted && !sm.abort_flag && warp == 0 && outh) {
+            float bs, bt;
+            int bc;
+            reduce_best(sm, kTwWarps, lane, bs, bc, bt);
+            const int64_t row = row0 + (h ? n1 : n0);
+            P.best_idx[row] = bc;
+            P.best_S[row] = bs;
+            P.stack[row] = bt;
+            if (P.best_param) P.best_param[row] = P.C[bc];
+        }
+        consumer_bar(32 * kTwWarps);                 // the arrays are reused
     }
 }
 
@@ -284,7 +357,7 @@ cudaError_t launch_t0win_w(SearchParams p, int max_rows, cudaStream_t stream) {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    constexpr int kT = 32 - 2 * (W / 2);
+    constexpr int kT = 64 - 2 * (W / 2);
     p.tiles_per_owner = (max_rows + kT - 1) / kT;
     const int64_t grid = p.nowner * (int64_t)p.tiles_per_owner;
     if (grid <= 0) return cudaSuccess;
