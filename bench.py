@@ -567,9 +567,24 @@ def run_t0win(args, torch, dist, seis, synth, rank, world, dev):
     strong = out_p["best_S"] >= 0.1
     same_strong = ((out_t["best_idx"] == out_p["best_idx"]) & strong).sum().item() / max(
         1, strong.sum().item())
+    ngathers = g.ngathers
+    del g, out_t, out_p
+    # CRS: 64 central CMPs of the crs-line workload, 21 x 21 x 41
+    dc = synth.workload_crs_line(seed=3 + 1000 * rank)
+    gc = seis.to_device(dc, dev)
+    ap = seis.crs_aperture(gc, dc["central"][:64], dc["apm"])
+    A, B, Cc = _crs_grids(torch, dev, synth, 21, 21, 41)
+    apt = seis.crs_aperture(gc, dc["central"][:4], dc["apm"])
+    seis.autotune_crs(gc, apt, A, B, Cc, w=W, reps=1)
+    seis.crs_semblance_t0win(gc, ap, A, B, Cc, w=W)
+    torch.cuda.synchronize()
+    _, crs_t = _time_steps(torch, stream, lambda: seis.crs_semblance_t0win(gc, ap, A, B, Cc, w=W), 2)
+    _, crs_p = _time_steps(torch, stream, lambda: seis.crs_semblance(gc, ap, A, B, Cc, w=W), 1)
+    seis.device_status()
+    crs_inter = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 1500 * 21 * 21 * 41
     return _simple_line("CMP t0-window semblance intersections/s", inter * world / (ms / 1e3),
                         ms, args, world,
-                        {"workload": f"cmp-line: {g.ngathers} gathers x fold 60 x 2000 samples "
+                        {"workload": f"cmp-line: {ngathers} gathers x fold 60 x 2000 samples "
                                      "@4ms, 201 C, w=11; window over neighbouring output times "
                                      "(one interpolated sample per intersection)",
                          "intersections_per_step": inter * world},
@@ -577,8 +592,12 @@ def run_t0win(args, torch, dist, seis, synth, rank, world, dev):
                          "paper_window_ms": total_p, "speedup_vs_paper_window": total_p / ms,
                          "rows_same_pick_as_paper_window": same,
                          "rows_pick_within_2_candidates": near,
-                         "rows_same_pick_where_paper_S_ge_0.1": same_strong},
-                        clk, args.steps)
+                         "rows_same_pick_where_paper_S_ge_0.1": same_strong,
+                         "crs_64_centrals": {"t0_window_ms": crs_t / 2, "paper_window_ms": crs_p,
+                                             "speedup": crs_p / (crs_t / 2),
+                                             "t0_window_intersections_per_s":
+                                                 crs_inter / (crs_t / 2e3)}},
+                        clk, args.steps + 3)
 
 
 def run_pragmatic(args, torch, dist, seis, synth, rank, world, dev):

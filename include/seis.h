@@ -158,6 +158,15 @@ int cmp_semblance_t0win(const seis_gathers* d, const float* C, int32_t nc, int32
                         float* S_cube, int32_t* best_idx, float* best_C, float* best_S,
                         float* stack_out, void* stream);
 
+/* CRS semblance with the window over neighbouring output times: cmp_semblance_t0win's
+ * definition with the CRS traveltime t = sqrt((t0' + A dm)^2 + B dm^2 + C h^2) of Section
+ * 2.2 over the aperture's traces (a trace also needs t0' + A dm >= 0 and a real t).
+ * Arguments, layouts and errors as crs_semblance (one launch; no workspace). */
+int crs_semblance_t0win(const seis_gathers* d, const seis_aperture* ap, const float* A,
+                        int32_t nA, const float* B, int32_t nB, const float* C, int32_t nC,
+                        int32_t w, float* S_cube, int32_t* best_idx, float* best_ABC,
+                        float* best_S, float* stack_out, void* stream);
+
 /* CRS aperture build -- Section 2.2 (the central CDP uses the traces of the CDPs within
  * radius r) and Section 3.5 (each CDP draws a circle around its midpoint).  For each
  * central gather central[c] (device int32 [n_central]) lists, in increasing order, every

@@ -61,6 +61,7 @@ def _load():
             lib.seis_oracle_cmp.restype = ctypes.c_int
             lib.seis_oracle_cmp_t0win.restype = ctypes.c_int
             lib.seis_oracle_crs.restype = ctypes.c_int
+            lib.seis_oracle_crs_t0win.restype = ctypes.c_int
             lib.seis_oracle_crs_eval.restype = ctypes.c_int
             lib.seis_oracle_crs_refine.restype = ctypes.c_int
             lib.seis_oracle_neighbours.restype = ctypes.c_int
@@ -178,9 +179,10 @@ def _crs_common(ds, nb):
 
 
 def crs_semblance(ds, nb, A, B, C, w=11, rows=None, want_cube=False, knot_eps=1e-3,
-                  nthreads=0) -> Result:
+                  nthreads=0, t0_window=False) -> Result:
     """CRS search over the flattened grid cand = (ia*nB + ib)*nC + ic.  ``nb`` =
-    (nbr_off, nbr_trace, m_c, out_off_c, dt_c) describes the central CDPs."""
+    (nbr_off, nbr_trace, m_c, out_off_c, dt_c) describes the central CDPs.  t0_window: the
+    window over neighbouring output times (reading c18, seis_oracle_crs_t0win)."""
     lib = _load()
     arrs = _crs_common(ds, nb)
     A = _c(A, np.float32); B = _c(B, np.float32); C = _c(C, np.float32)
@@ -195,7 +197,8 @@ def crs_semblance(ds, nb, A, B, C, w=11, rows=None, want_cube=False, knot_eps=1e
     bs = np.empty(nrows, np.float64)
     b2 = np.empty(nrows, np.float64)
     st = np.empty(nrows, np.float64)
-    rc = lib.seis_oracle_crs(*[_p(a) for a in arrs], ctypes.c_int64(ncen),
+    fn = lib.seis_oracle_crs_t0win if t0_window else lib.seis_oracle_crs
+    rc = fn(*[_p(a) for a in arrs], ctypes.c_int64(ncen),
                              _p(A), ctypes.c_int32(len(A)), _p(B), ctypes.c_int32(len(B)),
                              _p(C), ctypes.c_int32(len(C)), ctypes.c_int32(w),
                              _p(rows_a), ctypes.c_int64(nrows),

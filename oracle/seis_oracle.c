@@ -417,6 +417,92 @@ int seis_oracle_crs(const float* traces, const int64_t* trace_off, const float* 
 }
 
 /* ------------------------------------------------------------------------- */
+/* t0-window CRS semblance (reading c18 with the CRS traveltime of Section 2.2): as
+ * seis_oracle_cmp_t0win, the window running over the central's output times t0' =
+ * (n + j) dt, every aperture trace giving one interpolated sample at the traveltime
+ * sqrt((t0' + A dm)^2 + B dm^2 + C h^2) when t0' + A dm >= 0, the radicand >= 0 and both
+ * interpolation samples lie inside the trace.  Same outputs as seis_oracle_crs. */
+int seis_oracle_crs_t0win(const float* traces, const int64_t* trace_off, const float* h,
+                          const float* m, const int64_t* nbr_off, const int32_t* nbr_trace,
+                          const float* m_c, const int64_t* out_off_c, const float* dt_c,
+                          int64_t n_central,
+                          const float* A, int32_t nA, const float* B, int32_t nB,
+                          const float* C, int32_t nC, int32_t w,
+                          const int64_t* rows, int64_t nrows,
+                          double* S, int32_t* Nvalid, int8_t* edge,
+                          int32_t* best_idx, double* best_S, double* second_S, double* stack,
+                          double knot_eps, int32_t nthreads)
+{
+    if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || nA < 1 || nB < 1 || nC < 1 || n_central < 1)
+        return -1;
+    const int hw = w / 2;
+    const int64_t ncand = (int64_t)nA * nB * nC;
+    if (!rows) nrows = out_off_c[n_central];
+    set_threads(nthreads);
+
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t e = 0; e < nrows; ++e) {
+        const int64_t r = rows ? rows[e] : e;
+        const int64_t c = owner_of(out_off_c, n_central, r);
+        const int64_t n = r - out_off_c[c];
+        const int64_t nrow_c = out_off_c[c + 1] - out_off_c[c];
+        const double dtg = (double)dt_c[c];
+        const double mc = (double)m_c[c];
+        int32_t bi = -1; double bs = -1.0, b2 = -1.0, bst = 0.0;
+        for (int64_t cand = 0; cand < ncand; ++cand) {
+            const double Av = (double)A[cand / ((int64_t)nB * nC)];
+            const double Bv = (double)B[(cand / nC) % nB];
+            const double Cv = (double)C[cand % nC];
+            double num = 0.0, den = 0.0, s0 = 0.0; int64_t M0 = 0; int flag = 0;
+            for (int j = -hw; j <= hw; ++j) {
+                const int64_t n2 = n + j;
+                if (n2 < 0 || n2 >= nrow_c) continue;
+                const double t0 = (double)n2 * dtg;
+                double sj = 0.0, ej = 0.0; int64_t Mj = 0;
+                for (int64_t q = nbr_off[c]; q < nbr_off[c + 1]; ++q) {
+                    const int64_t i = nbr_trace[q];
+                    const double dm = (double)m[i] - mc;
+                    const double hi = (double)h[i];
+                    const int64_t ns_i = trace_off[i + 1] - trace_off[i];
+                    const double rad = (t0 + Av * dm) * (t0 + Av * dm) + Bv * dm * dm + Cv * hi * hi;
+                    const int exact = zero_moveout(Av, Bv, Cv, dm, hi);
+                    if (edge && ((Av * dm != 0.0 && fabs(t0 + Av * dm) < knot_eps * dtg) ||
+                                 (!exact && fabs(rad) < knot_eps * dtg * dtg)))
+                        flag = 1;
+                    double u, p;
+                    if (!crs_time(t0, Av, Bv, Cv, dm, hi, dtg, &u, &p, NULL)) continue;
+                    if (edge && !exact &&
+                        sample_inside(u - knot_eps, ns_i) != sample_inside(u + knot_eps, ns_i))
+                        flag = 1;
+                    if (!sample_inside(u, ns_i)) continue;
+                    const int64_t k = (int64_t)floor(u);
+                    const double x = u - (double)k;
+                    const float* f = traces + trace_off[i];
+                    const double v = ((double)f[k + 1] - (double)f[k]) * x + (double)f[k];
+                    sj += v;
+                    ej += v * v;
+                    ++Mj;
+                }
+                num += sj * sj;
+                den += (double)Mj * ej;
+                if (j == 0) { s0 = sj; M0 = Mj; }
+            }
+            const double sv = (den > 0.0) ? num / den : 0.0;
+            if (S) S[e * ncand + cand] = sv;
+            if (Nvalid) Nvalid[e * ncand + cand] = (int32_t)M0;
+            if (edge) edge[e * ncand + cand] = (int8_t)flag;
+            if (sv > bs) { b2 = bs; bs = sv; bi = (int32_t)cand; bst = M0 ? s0 / (double)M0 : 0.0; }
+            else if (sv > b2) b2 = sv;
+        }
+        if (best_idx) best_idx[e] = bi;
+        if (best_S) best_S[e] = bs;
+        if (second_S) second_S[e] = b2;
+        if (stack) stack[e] = bst;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Semblance, stack and analytic gradient of one CRS operator per output row (readings
  * c8 and c15).  theta[e*3 + {0,1,2}] = (A, B, C) for evaluated row e.  CMP is the case
  * A = B = 0 with the gather's own traces as the neighbour list.

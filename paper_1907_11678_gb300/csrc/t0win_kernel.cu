@@ -1,5 +1,5 @@
-// t0win_kernel.cu -- CMP semblance with the window over neighbouring output times
-// (cmp_semblance_t0win).  Not the paper's method: Algorithm 1 reads w samples along each
+// t0win_kernel.cu -- CMP and CRS semblance with the window over neighbouring output times
+// (cmp_semblance_t0win, crs_semblance_t0win).  Not the paper's method: Algorithm 1 reads w samples along each
 // trace around its own intersection, so every (row, candidate, trace) costs w
 // interpolations; here the window runs over the output times t0' = t0 + j dt, each with its
 // own traveltime (Section 2.1), so every (row, candidate, trace) costs one interpolation and
@@ -32,7 +32,7 @@ constexpr int kTwThreads = 32 * (kTwWarps + 1);
 struct TwAccum {
     f2_t s2[kTwR], e2[kTwR];
     int M0[kTwR], M1[kTwR];
-    f2_t C2[kTwR];
+    float Ar[kTwR], Br[kTwR], Cr[kTwR];    // CMP: A = B = 0
     int cidx[kTwR];
 };
 
@@ -42,10 +42,11 @@ struct TwRows {
 };
 
 // One interpolated sample per (row pair, candidate, trace) of a run of traces [t0, t1):
-// the traveltime pair D = Cq / (sqrt(n^2 + Cq) + n) in f32x2, floor and fraction by the
-// rounding shift, then v = f[k] + x (f[k+1] - f[k]).  The traveltimes of trace t+1 are
-// formed while trace t is interpolated.
-template <bool FAST>
+// the moveout pair in samples, D = Cq / (sqrt(n^2 + Cq) + n) (CMP) or
+// D = a + r / (sqrt(p^2 + r) + p) with a = A e, p = n + a, r = B g + C q (CRS), in f32x2,
+// floor and fraction by the rounding shift, then v = f[k] + x (f[k+1] - f[k]).  The
+// traveltimes of trace t+1 are formed while trace t is interpolated.
+template <bool CRS, bool FAST>
 __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0, int t1,
                                        int slot_base, const TwRows& rw, int zidx,
                                        const float* smf) {
@@ -55,21 +56,41 @@ __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0
     const f2_t shift2 = pk2(kFloorShift, kFloorShift);
     auto setup = [&](int t) {
         const TraceMeta& tm = meta[t];
-        const f2_t q2 = pk2(tm.q, tm.q);
         const unsigned rng = (unsigned)(tm.kmax - tm.kmin);
         const int kbase = slot_base + tm.base + tm.kmin;
         const int off0 = rw.n0 - kFloorShiftBits - tm.kmin;
         const int off1 = rw.n1 - kFloorShiftBits - tm.kmin;
         #pragma unroll
         for (int r = 0; r < kTwR; ++r) {
-            const f2_t cq2 = mul2(a.C2[r], q2);
-            const f2_t rad2 = add2(rw.nsq2, cq2);
-            float ra, rb;
-            up2(rad2, ra, rb);
-            const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), rw.nf2);
-            float sa, sb;
-            up2(sum2, sa, sb);
-            const f2_t D2 = mul2(cq2, pk2(rcp_fast(sa), rcp_fast(sb)));
+            f2_t D2;
+            bool p0 = true, p1 = true;
+            if constexpr (CRS) {
+                const float av = a.Ar[r] * tm.e;
+                const float rr = fmaf(a.Br[r], tm.g, a.Cr[r] * tm.q);
+                const f2_t a2 = pk2(av, av), rr2 = pk2(rr, rr);
+                const f2_t pp2 = add2(rw.nf2, a2);
+                const f2_t rad2 = fma2(pp2, pp2, rr2);
+                float ra, rb, pa, pb;
+                up2(rad2, ra, rb);
+                up2(pp2, pa, pb);
+                p0 = pa >= 0.f;
+                p1 = pb >= 0.f;
+                const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), pp2);
+                float sa, sb;
+                up2(sum2, sa, sb);
+                if constexpr (!FAST) { sa = fmaxf(sa, 1e-30f); sb = fmaxf(sb, 1e-30f); }
+                D2 = fma2(rr2, pk2(rcp_fast(sa), rcp_fast(sb)), a2);
+            } else {
+                const float cq = a.Cr[r] * tm.q;
+                const f2_t cq2 = pk2(cq, cq);
+                const f2_t rad2 = add2(rw.nsq2, cq2);
+                float ra, rb;
+                up2(rad2, ra, rb);
+                const f2_t sum2 = add2(pk2(sqrt_fast(ra), sqrt_fast(rb)), rw.nf2);
+                float sa, sb;
+                up2(sum2, sa, sb);
+                D2 = mul2(cq2, pk2(rcp_fast(sa), rcp_fast(sb)));
+            }
             const f2_t tt2 = add2_rm(D2, shift2);
             f2_t x2 = sub2(D2, sub2(tt2, shift2));
             float ta, tb;
@@ -81,7 +102,7 @@ __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0
                 sI1[r] = kbase + (int)min((unsigned)kk1, rng);
                 sO0[r] = sO1[r] = true;
             } else {
-                const bool ok0 = (unsigned)kk0 <= rng, ok1 = (unsigned)kk1 <= rng;
+                const bool ok0 = p0 && (unsigned)kk0 <= rng, ok1 = p1 && (unsigned)kk1 <= rng;
                 float xa, xb;
                 up2(x2, xa, xb);
                 x2 = pk2(ok0 ? xa : 0.f, ok1 ? xb : 0.f);   // a NaN fraction must not reach the sums
@@ -146,7 +167,7 @@ __device__ __forceinline__ void window_sums2(float s_lo, float s_hi, float m_lo,
     }
 }
 
-template <int W>
+template <bool CRS, int W>
 __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams P) {
     constexpr int HW = W / 2;
     constexpr int kT = 64 - 2 * HW;              // output rows per CTA
@@ -184,8 +205,9 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
         // =============================== producer warp ================================
         const int n_first = max(base, 0);
         const int n_last = min(base + 63, nrows - 1);
+        const float mc = CRS ? P.m_c[owner] : 0.f;
         int pl_pass = 0, pl_t = 0, pl_bpass = -1;
-        float bC0 = 0.f, bC1 = 0.f;
+        float bA0 = 0.f, bA1 = 0.f, bB0 = 0.f, bB1 = 0.f, bC0 = 0.f, bC1 = 0.f;
         int s = 0;
         for (;; ++s) {
             const int slot = s % kSlots;
@@ -202,21 +224,23 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
                 mbar_arrive(&sm.full[slot]);
                 break;
             }
-            if (pl_bpass != pl_pass) {   // C bounds of the pass (one candidate per lane)
+            if (pl_bpass != pl_pass) {   // candidate bounds of the pass (one per lane)
                 const int c = pl_pass * kTwCB + lane;
                 const bool v = lane < kTwCB && c < P.ncand;
-                const float cc = v ? P.C[c] : 0.f;
-                bC0 = warp_min(v ? cc : FLT_MAX);
-                bC1 = warp_max(v ? cc : -FLT_MAX);
+                float av = 0.f, bv = 0.f, cc = 0.f;
+                if (v) decode_candidate<CRS>(P, c, av, bv, cc);
+                bA0 = warp_min(v ? av : FLT_MAX);  bA1 = warp_max(v ? av : -FLT_MAX);
+                bB0 = warp_min(v ? bv : FLT_MAX);  bB1 = warp_max(v ? bv : -FLT_MAX);
+                bC0 = warp_min(v ? cc : FLT_MAX);  bC1 = warp_max(v ? cc : -FLT_MAX);
                 pl_bpass = pl_pass;
             }
             const int first = (pl_t == 0);
             int nfit = 0;
             unsigned allv = 0u;
-            const int ntr = produce_stage<false, 0>(
+            const int ntr = produce_stage<CRS, 0>(
                 sm.buf[slot], sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h,
-                nullptr, P.list, lbeg, M, pl_t, dt, 0.f, n_first, n_last,
-                StageBounds{0.f, 0.f, 0.f, 0.f, bC0, bC1}, P.status, nfit, allv);
+                CRS ? P.m : nullptr, P.list, lbeg, M, pl_t, dt, mc, n_first, n_last,
+                StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit, allv);
             pl_t += nfit;
             const int last = (pl_t >= M);
             if (lane == 0) sm.desc[slot] = make_desc(pl_pass, ntr, allv, first, last, 0);
@@ -269,9 +293,9 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
             #pragma unroll
             for (int r = 0; r < kTwR; ++r) {
                 const int c = d.pass * kTwCB + warp * kTwR + r;
-                const float cc = c < P.ncand ? P.C[c] : 0.f;
+                a.Ar[r] = a.Br[r] = a.Cr[r] = 0.f;
+                if (c < P.ncand) decode_candidate<CRS>(P, c, a.Ar[r], a.Br[r], a.Cr[r]);
                 a.cidx[r] = c;
-                a.C2[r] = pk2(cc, cc);
                 a.s2[r] = 0ull;
                 a.e2[r] = 0ull;
                 a.M0[r] = a.M1[r] = 0;
@@ -286,8 +310,8 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
                 const unsigned rest = (fast ? ~d.allv : d.allv) >> t;
                 const int len = rest ? __ffs(rest) - 1 : 32;
                 const int t1 = min(ntr, t + len);
-                if (fast) tw_run<true>(a, sm.meta[slot], t, t1, slot_base, rw, zidx, smf);
-                else tw_run<false>(a, sm.meta[slot], t, t1, slot_base, rw, zidx, smf);
+                if (fast) tw_run<CRS, true>(a, sm.meta[slot], t, t1, slot_base, rw, zidx, smf);
+                else tw_run<CRS, false>(a, sm.meta[slot], t, t1, slot_base, rw, zidx, smf);
                 t = t1;
             }
         }
@@ -338,13 +362,23 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
             P.best_idx[row] = bc;
             P.best_S[row] = bs;
             P.stack[row] = bt;
-            if (P.best_param) P.best_param[row] = P.C[bc];
+            if (P.best_param) {
+                float av, bv, cc;
+                decode_candidate<CRS>(P, bc, av, bv, cc);
+                if (CRS) {
+                    P.best_param[row * 3 + 0] = av;
+                    P.best_param[row * 3 + 1] = bv;
+                    P.best_param[row * 3 + 2] = cc;
+                } else {
+                    P.best_param[row] = cc;
+                }
+            }
         }
         consumer_bar(32 * kTwWarps);                 // the arrays are reused
     }
 }
 
-template <int W>
+template <bool CRS, int W>
 cudaError_t launch_t0win_w(SearchParams p, int max_rows, cudaStream_t stream) {
     static bool configured[64] = {};
     const int smem = (int)sizeof(SearchSmem);
@@ -352,8 +386,8 @@ cudaError_t launch_t0win_w(SearchParams p, int max_rows, cudaStream_t stream) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(t0win_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem);
+        e = cudaFuncSetAttribute(t0win_kernel<CRS, W>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
@@ -362,22 +396,23 @@ cudaError_t launch_t0win_w(SearchParams p, int max_rows, cudaStream_t stream) {
     const int64_t grid = p.nowner * (int64_t)p.tiles_per_owner;
     if (grid <= 0) return cudaSuccess;
     if (grid > INT_MAX) return cudaErrorInvalidValue;
-    t0win_kernel<W><<<(unsigned)grid, kTwThreads, smem, stream>>>(p);
+    t0win_kernel<CRS, W><<<(unsigned)grid, kTwThreads, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_t0win(const SearchParams& p, int w, int max_rows, cudaStream_t s) {
+template <bool CRS>
+cudaError_t launch_t0win_c(const SearchParams& p, int w, int max_rows, cudaStream_t s) {
     switch (w) {
-        case 1: return launch_t0win_w<1>(p, max_rows, s);
-        case 3: return launch_t0win_w<3>(p, max_rows, s);
-        case 5: return launch_t0win_w<5>(p, max_rows, s);
-        case 7: return launch_t0win_w<7>(p, max_rows, s);
-        case 9: return launch_t0win_w<9>(p, max_rows, s);
-        case 11: return launch_t0win_w<11>(p, max_rows, s);
-        case 13: return launch_t0win_w<13>(p, max_rows, s);
-        case 15: return launch_t0win_w<15>(p, max_rows, s);
+        case 1: return launch_t0win_w<CRS, 1>(p, max_rows, s);
+        case 3: return launch_t0win_w<CRS, 3>(p, max_rows, s);
+        case 5: return launch_t0win_w<CRS, 5>(p, max_rows, s);
+        case 7: return launch_t0win_w<CRS, 7>(p, max_rows, s);
+        case 9: return launch_t0win_w<CRS, 9>(p, max_rows, s);
+        case 11: return launch_t0win_w<CRS, 11>(p, max_rows, s);
+        case 13: return launch_t0win_w<CRS, 13>(p, max_rows, s);
+        case 15: return launch_t0win_w<CRS, 15>(p, max_rows, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -393,7 +428,22 @@ extern "C" int cmp_semblance_t0win(const seis_gathers* d, const float* C, int32_
     TuneKey key;
     int rc = build_cmp_params(d, C, nc, w, S_cube, best_idx, best_C, best_S, stack_out, &p, &key);
     if (rc) return rc;
-    cudaError_t e = launch_t0win(p, w, d->max_rows, static_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_t0win_c<false>(p, w, d->max_rows, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "cmp_semblance_t0win launch");
+    return SEIS_OK;
+}
+
+extern "C" int crs_semblance_t0win(const seis_gathers* d, const seis_aperture* ap,
+                                   const float* A, int32_t nA, const float* B, int32_t nB,
+                                   const float* C, int32_t nC, int32_t w, float* S_cube,
+                                   int32_t* best_idx, float* best_ABC, float* best_S,
+                                   float* stack_out, void* stream) {
+    SearchParams p;
+    TuneKey key;
+    int rc = build_crs_params(d, ap, A, nA, B, nB, C, nC, w, S_cube, best_idx, best_ABC, best_S,
+                              stack_out, &p, &key);
+    if (rc) return rc;
+    cudaError_t e = launch_t0win_c<true>(p, w, ap->max_rows, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "crs_semblance_t0win launch");
     return SEIS_OK;
 }

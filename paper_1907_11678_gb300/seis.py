@@ -67,6 +67,7 @@ def load_library(path: str | None = None):
             lib.cmp_semblance_t0win.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
             lib.crs_semblance.argtypes = [vp, vp, vp, i32, vp, i32, vp, i32, i32,
                                           vp, vp, vp, vp, vp, vp]
+            lib.crs_semblance_t0win.argtypes = lib.crs_semblance.argtypes
             lib.seis_crs_aperture.argtypes = [vp, vp, i64, f32, vp, vp, i64, vp, vp, vp,
                                               vp, vp, vp, vp]
             lib.seis_search_variant_name.restype = ctypes.c_char_p
@@ -110,6 +111,7 @@ def load_library(path: str | None = None):
                          "crs_semblance_grad", "crs_refine", "crs_top_starts",
                          "crs_refine_multi", "seis_batch_semblance", "seis_autotune_batch",
                          "seis_crs_aperture_offset", "crs_pragmatic", "cmp_semblance_t0win",
+                         "crs_semblance_t0win",
                          "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -284,10 +286,7 @@ def crs_aperture(g: Gathers, central, apm: float, hmax: float | None = None,
     return Aperture(nbr_off, nbr_trace, m_c, out_off, dt_c, n, int(mr.value), int(rows.value))
 
 
-def crs_semblance(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor,
-                  w: int = 11, want_cube: bool = False, stream=None) -> dict:
-    """CRS semblance search over the flattened A x B x C grid (include/seis.h:
-    crs_semblance).  Returns best_idx, best_ABC [rows, 3], best_S, stack (and S)."""
+def _crs_search(lib_fn, g, ap, A, B, C, w, want_cube, stream) -> dict:
     lib = load_library()
     dev = g.traces.device
     nA, nB, nC = int(A.numel()), int(B.numel()), int(C.numel())
@@ -297,12 +296,27 @@ def crs_semblance(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor, C:
                stack=torch.empty(ap.rows, dtype=torch.float32, device=dev))
     if want_cube:
         out["S"] = torch.empty((ap.rows, nA * nB * nC), dtype=torch.float32, device=dev)
-    rc = lib.crs_semblance(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
-                           _ptr(A), nA, _ptr(B), nB, _ptr(C), nC, w, _ptr(out.get("S")),
-                           _ptr(out["best_idx"]), _ptr(out["best_ABC"]), _ptr(out["best_S"]),
-                           _ptr(out["stack"]), _stream_handle(stream))
+    rc = getattr(lib, lib_fn)(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
+                              _ptr(A), nA, _ptr(B), nB, _ptr(C), nC, w, _ptr(out.get("S")),
+                              _ptr(out["best_idx"]), _ptr(out["best_ABC"]), _ptr(out["best_S"]),
+                              _ptr(out["stack"]), _stream_handle(stream))
     _check(rc)
     return out
+
+
+def crs_semblance(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor,
+                  w: int = 11, want_cube: bool = False, stream=None) -> dict:
+    """CRS semblance search over the flattened A x B x C grid (include/seis.h:
+    crs_semblance).  Returns best_idx, best_ABC [rows, 3], best_S, stack (and S)."""
+    return _crs_search("crs_semblance", g, ap, A, B, C, w, want_cube, stream)
+
+
+def crs_semblance_t0win(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor,
+                        C: torch.Tensor, w: int = 11, want_cube: bool = False,
+                        stream=None) -> dict:
+    """CRS search with the window over neighbouring output times (include/seis.h:
+    crs_semblance_t0win).  Same outputs as crs_semblance."""
+    return _crs_search("crs_semblance_t0win", g, ap, A, B, C, w, want_cube, stream)
 
 
 def search_variants() -> list[str]:

@@ -198,3 +198,25 @@ def test_crs_pragmatic_matches_oracle(seis):
     print(f"[parity] pragmatic CRS: rows compared {ok.mean():.3f}, max dS {dS:.2e}, "
           f"stack rel L2 {rel:.2e}")
     assert dS <= parity.S_TOL and rel <= parity.STACK_TOL
+
+
+@pytest.mark.parametrize("w", [3, 11])
+def test_crs_t0win_matches_oracle(seis, w):
+    """CRS with the window over neighbouring output times (64-row blocks, halo lanes)."""
+    ds = synth.crs_line(9, 10, 230, 0.004, 0.0, 1500.0, 2, 1, 2.0, seed=81 + w)
+    g = seis.to_device(ds)
+    ap = seis.crs_aperture(g, [2, 4, 6], 25.0)
+    nb = oracle.aperture(ds, [2, 4, 6], 25.0)
+    A, B, C = _grids(5, 3, 7)
+    t = lambda a: torch.from_numpy(a).cuda()
+    out = seis.crs_semblance_t0win(g, ap, t(A), t(B), t(C), w=w, want_cube=True)
+    torch.cuda.synchronize()
+    seis.device_status()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    ref = oracle.crs_semblance(ds, nb, A, B, C, w=w, want_cube=True, t0_window=True)
+    parity.check_cube(got["S"], ref, f"crs t0win w{w}", max_exempt=w * parity.MAX_EXEMPT_SMALL)
+    parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, f"crs t0win w{w}",
+                       row_edge=(ref.edge != 0).any(axis=1))
+    ia, rem = np.divmod(got["best_idx"], 3 * 7)
+    ib, ic = np.divmod(rem, 7)
+    np.testing.assert_array_equal(got["best_ABC"], np.stack([A[ia], B[ib], C[ic]], 1))

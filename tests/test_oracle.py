@@ -461,6 +461,32 @@ def test_t0win_invariants():
     assert np.all(oracle.cmp_semblance(zero, C, t0_window=True).S == 0)
 
 
+def test_crs_t0win_reduces_to_cmp_t0win():
+    """dm = 0 (each gather its own aperture) and A = B = 0: the CRS t0-window search is the
+    CMP one, bit for bit (the same FP64 operations)."""
+    rng = np.random.default_rng(31)
+    ds = dataset([rng.normal(size=180) for _ in range(10)], np.tile(np.linspace(0, 900, 5), 2),
+                 0.004, gather_sizes=[5, 5])
+    C = np.float32(np.linspace(0, 2e-6, 7))
+    a = oracle.cmp_semblance(ds, C, w=9, t0_window=True)
+    b = oracle.crs_semblance(ds, oracle.cmp_as_crs(ds), [0.0], [0.0], C, w=9, want_cube=True,
+                             t0_window=True)
+    np.testing.assert_array_equal(a.S, b.S)
+    np.testing.assert_array_equal(a.best_idx, b.best_idx)
+    np.testing.assert_array_equal(a.stack, b.stack)
+
+
+def test_crs_t0win_constant_traces():
+    ds = dataset([np.full(150, -0.8) for _ in range(9)], np.tile([0, 300, 600], 3), 0.004,
+                 m=np.repeat([0.0, 12.5, 25.0], 3), gather_sizes=[3, 3, 3])
+    nb = oracle.aperture(ds, [1], 12.5)
+    r = oracle.crs_semblance(ds, nb, [-1e-4, 0, 1e-4], [0.0, 1e-7], [0.0, 1e-6], w=5,
+                             want_cube=True, t0_window=True)
+    live = r.N > 0
+    assert live.mean() > 0.5
+    np.testing.assert_allclose(r.S[live], 1.0, rtol=0, atol=1e-14)
+
+
 def test_invalid_arguments():
     ds = dataset([np.zeros(50)], [0.0], 0.004)
     with pytest.raises(ValueError):
