@@ -823,7 +823,8 @@ def main():
                     help="gathers per GPU (4096 = the benchmark workload; fewer only for profiling)")
     ap.add_argument("--centrals", type=int, default=1024, help="crs-line: central CMPs")
     ap.add_argument("--items", type=int, default=10000, help="batch: items")
-    ap.add_argument("--dense-centrals", type=int, default=16, help="refine: dense-grid slice")
+    ap.add_argument("--dense-centrals", type=int, default=24,
+                    help="refine: dense-grid slice (24 x 63 tiles = 4.97 waves of 304 CTAs)")
     ap.add_argument("--starts", type=int, default=16, help="refine: coarse starts per row")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
     ap.add_argument("--variant", type=int, default=None,

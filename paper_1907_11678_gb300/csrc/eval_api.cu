@@ -145,14 +145,14 @@ int refine_run(const EvalParams& p0, float* theta, const float* lo3, const float
     cudaError_t e = launch_eval(p, true, true, w, s);
     if (e != cudaSuccess) return cuda_fail(e, "crs_refine eval");
     u.init = 1;
-    u.judge = 0;
+    u.assess = 0;
     u.propose = steps > 0;
     if ((e = launch_refine_update(u, s)) != cudaSuccess) return cuda_fail(e, "crs_refine update");
     u.init = 0;
     p.theta = trial_theta;
     for (int it = 0; it < steps; ++it) {
         if ((e = launch_eval(p, true, true, w, s)) != cudaSuccess) return cuda_fail(e, "crs_refine eval");
-        u.judge = 1;
+        u.assess = 1;
         u.propose = it + 1 < steps;
         if ((e = launch_refine_update(u, s)) != cudaSuccess) return cuda_fail(e, "crs_refine update");
     }

@@ -243,7 +243,7 @@ __device__ __forceinline__ void h_mul(const float* H, const float* v, float* o) 
     o[2] = H[2] * v[0] + H[4] * v[1] + H[5] * v[2];
 }
 
-// One refinement step per row: judge the evaluated trial, then propose the next one.  The
+// One refinement step per row: assess the evaluated trial, then propose the next one.  The
 // rule is a projected quasi-Newton (BFGS) ascent of S in normalised coordinates
 // z = (theta - lo) / (hi - lo) with step halving on a failed trial:
 //   d = H g (H reset to (step0/|g|) I when d is not an ascent direction), |d| <= 0.25,
@@ -268,7 +268,7 @@ __global__ void refine_update_kernel(const RefineParams R) {
         h_reset(H, gz, R.step0);
     } else {
         for (int i = 0; i < 6; ++i) H[i] = R.H[r * 6 + i];
-        if (R.judge && al > 0.f) {
+        if (R.assess && al > 0.f) {
             if (R.trial_S[r] >= R.S[r]) {
                 float sv[3], yv[3], ss = 0.f, yy = 0.f, sy = 0.f;
                 for (int a = 0; a < 3; ++a) {

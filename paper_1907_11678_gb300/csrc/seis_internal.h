@@ -64,7 +64,7 @@ struct EvalParams {
 
 // One refinement step per row (reading c16: projected normalised-gradient ascent).  State:
 // theta/S/grad/stack = accepted point, trial_* = the last evaluated trial, step (< 0 once
-// the gradient vanished: no further trials).  If `judge`, the trial is accepted when its S is
+// the gradient vanished: no further trials).  If `assess`, the trial is accepted when its S is
 // not lower, else the step halves.  If `propose`, the next trial is formed.
 struct RefineParams {
     int64_t rows;
@@ -80,7 +80,7 @@ struct RefineParams {
     float* H;       // [rows][6] inverse curvature estimates (symmetric 3x3)
     float lo[3], hi[3];
     float step0;
-    int judge, propose, init;
+    int assess, propose, init;
 };
 
 // Launchers (return the cudaError_t of the launch).
