@@ -300,30 +300,66 @@ def run_cmp_line(args, torch, dist, seis, synth, rank, world, dev):
     return line
 
 
+E2E_CHUNKS = 8
+
+
 def _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream, torch, dist, seis):
     """Same metric through the C ABI with the step's inputs copied from pinned host
-    memory and its results copied back inside the timed region."""
-    host = {k: torch.from_numpy(np.ascontiguousarray(ds[k])).pin_memory()
-            for k in ("traces", "trace_off", "h", "gather_off", "out_off", "dt")}
-    dev_bufs = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    memory and its results copied back inside the timed region.  The gathers stream in
+    E2E_CHUNKS chunks over two streams: chunk c+1's inputs travel while chunk c is searched,
+    and each chunk's results return as soon as it is done."""
+    G = g.ngathers
+    gb = [G * c // E2E_CHUNKS for c in range(E2E_CHUNKS + 1)]
+    goff = np.asarray(ds["gather_off"], np.int64)
+    toff = np.asarray(ds["trace_off"], np.int64)
+    ooff = np.asarray(ds["out_off"], np.int64)
+    chunks = []
+    for c in range(E2E_CHUNKS):
+        g0, g1 = gb[c], gb[c + 1]
+        t0, t1 = int(goff[g0]), int(goff[g1])
+        s0, s1 = int(toff[t0]), int(toff[t1])
+        r0, r1 = int(ooff[g0]), int(ooff[g1])
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        host = {"traces": pin(ds["traces"][s0:s1]), "trace_off": pin(toff[t0:t1 + 1] - s0),
+                "h": pin(ds["h"][t0:t1]), "gather_off": pin(goff[g0:g1 + 1] - t0),
+                "out_off": pin(ooff[g0:g1 + 1] - r0), "dt": pin(ds["dt"][g0:g1])}
+        devb = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+        gc = seis.Gathers(traces=devb["traces"], trace_off=devb["trace_off"], h=devb["h"],
+                          m=None, gather_off=devb["gather_off"], out_off=devb["out_off"],
+                          dt=devb["dt"], ngathers=g1 - g0, ntraces=t1 - t0,
+                          max_rows=g.max_rows, max_trace_samples=g.max_trace_samples,
+                          rows=r1 - r0)
+        outc = {k: v[r0:r1] for k, v in out.items()}
+        outh = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outc.items()}
+        chunks.append((host, devb, gc, outc, outh))
     Ch = torch.from_numpy(C).pin_memory()
-    outs_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
-    h2d = sum(v.numel() * v.element_size() for v in host.values()) + Ch.numel() * 4
-    d2h = sum(v.numel() * v.element_size() for v in out.values())
-    g2 = seis.Gathers(traces=dev_bufs["traces"], trace_off=dev_bufs["trace_off"],
-                      h=dev_bufs["h"], m=None, gather_off=dev_bufs["gather_off"],
-                      out_off=dev_bufs["out_off"], dt=dev_bufs["dt"], ngathers=g.ngathers,
-                      ntraces=g.ntraces, max_rows=g.max_rows,
-                      max_trace_samples=g.max_trace_samples, rows=g.rows)
     Cd2 = torch.empty_like(Cd)
+    h2d = sum(v.numel() * v.element_size() for ch in chunks for v in ch[0].values()) + Ch.numel() * 4
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    copy = torch.cuda.Stream(device=dev)
 
     def e2e_step():
-        for k in host:
-            dev_bufs[k].copy_(host[k], non_blocking=True)
-        Cd2.copy_(Ch, non_blocking=True)
-        seis.cmp_semblance(g2, Cd2, w=W, out=out)
-        for k in out:
-            outs_h[k].copy_(out[k], non_blocking=True)
+        copy.wait_stream(stream)                  # the previous step's readers are done
+        with torch.cuda.stream(copy):
+            Cd2.copy_(Ch, non_blocking=True)
+        ready = []
+        for host, devb, _, _, _ in chunks:        # all inputs, in chunk order
+            with torch.cuda.stream(copy):
+                for k in host:
+                    devb[k].copy_(host[k], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy)
+            ready.append(ev)
+        for (_, _, gc, outc, outh), ev in zip(chunks, ready):
+            stream.wait_event(ev)
+            seis.cmp_semblance(gc, Cd2, w=W, out=outc, stream=stream)
+            done = torch.cuda.Event()
+            done.record(stream)
+            copy.wait_event(done)
+            with torch.cuda.stream(copy):
+                for k in outc:
+                    outh[k].copy_(outc[k], non_blocking=True)
+        stream.wait_stream(copy)                  # the step ends when its results are home
     for _ in range(max(1, args.warmup)):
         e2e_step()
     torch.cuda.synchronize()
@@ -331,10 +367,11 @@ def _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream, torch, dist, seis):
         dist.barrier()
     _, total = _time_steps(torch, stream, e2e_step, args.steps)
     e2e_ms = _max_over_ranks(torch, dist, world, dev, total / args.steps)
-    assert np.array_equal(outs_h["best_idx"].numpy(), out["best_idx"].cpu().numpy())
+    got = np.concatenate([ch[4]["best_idx"].numpy() for ch in chunks])
+    assert np.array_equal(got, out["best_idx"].cpu().numpy())
     return {"value": inter * world * W / (e2e_ms / 1e3), "unit": "trace-samples/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": e2e_ms}
+            "ms_per_step": e2e_ms, "chunks": E2E_CHUNKS}
 
 
 # ------------------------------------------------------------------ the other workloads ----

@@ -189,3 +189,29 @@ def test_t0win_cmp_small_workload(seis):
     rep = _check_t0win(seis, ds, _grid(101), 11, "t0win cmp-small",
                        max_exempt=11 * parity.MAX_EXEMPT)
     assert rep["pick_agree"] > 0.99
+
+
+def test_t0win_ragged_gathers_empty_and_fold_one(seis):
+    """The t0-window search on gathers of different fold, output length and dt, with an
+    empty gather and a fold-1 gather (whose rows all have S = 1 where the trace takes part)."""
+    rng = np.random.default_rng(8)
+    traces, h, sizes, outs, dts = [], [], [], [], []
+    spec = [(9, 77, 0.004), (0, 40, 0.004), (1, 130, 0.002), (17, 301, 0.002), (5, 33, 0.004)]
+    for fold, ns, dt in spec:
+        for i in range(fold):
+            L = ns + int(rng.integers(-20, 25)) if fold > 1 else ns
+            traces.append(rng.standard_normal(max(L, 1)).astype(np.float32))
+            h.append(rng.uniform(0, 1600))
+        sizes.append(fold); outs.append(ns); dts.append(dt)
+    ds = dataset(traces, h, 0.0, gather_sizes=sizes, out_ns=outs)
+    ds["dt"] = np.float32(dts)
+    _check_t0win(seis, ds, _grid(29), 7, "t0win ragged gathers")
+    g = seis.to_device(ds)
+    out = seis.cmp_semblance_t0win(g, torch.from_numpy(_grid(29)).cuda(), w=7, want_cube=True)
+    S = out["S"].cpu().numpy()
+    o = ds["out_off"]
+    assert np.all(S[o[1]:o[2]] == 0) and np.all(out["best_idx"][o[1]:o[2]].cpu().numpy() == 0)
+    ref = oracle.cmp_semblance(ds, _grid(29), w=7, t0_window=True)
+    one = slice(o[2], o[3])
+    live = ref.S[one] > 0
+    np.testing.assert_allclose(S[one][live], 1.0, atol=1e-6)
