@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
                 const float dj = F[j + 1] - F[j];
                 const float v = fmaf(x, dj, F[j]);
                 num[j] += v;
-                den[j & 1] = fmaf(v, v, den[j & 1]);
+                den[kDenChains == 2 ? (j & 1) : 0] = fmaf(v, v, den[kDenChains == 2 ? (j & 1) : 0]);
                 if (GRAD) {
                     vd = fmaf(v, dj, vd);
                     #pragma unroll
@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
     float dnu[3] = {0.f, 0.f, 0.f};
     #pragma unroll
     for (int j = 0; j < W; ++j) {
-        if (j & 1) nu1 = fmaf(num[j], num[j], nu1); else nu0 = fmaf(num[j], num[j], nu0);
+        if (kDenChains == 2 && (j & 1)) nu1 = fmaf(num[j], num[j], nu1);
+        else nu0 = fmaf(num[j], num[j], nu0);
         ac += num[j];
         if (GRAD) {
             #pragma unroll

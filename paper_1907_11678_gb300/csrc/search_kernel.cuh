@@ -155,6 +155,10 @@ __device__ __forceinline__ f2_t add2_rm(f2_t a, f2_t b) {
 // give huge positive or negative integers, which the range test rejects.
 constexpr float kFloorShift = 12582912.0f;     // 1.5 * 2^23
 constexpr int kFloorShiftBits = 0x4B400000;
+// FMA chains of the window energy (and of the numerator's sum of squares, summed in the same
+// order): 1 leaves the packed kernels two more registers (fewer spills in CRS) and costs the
+// scalar ones some ILP; every kernel uses the same value, so all stay bit-identical.
+constexpr int kDenChains = 1;
 
 __device__ __forceinline__ float warp_min(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
@@ -464,7 +468,7 @@ struct Accum {
     static constexpr int kR = CFG::kR;
     static constexpr int kG = kP ? kR / 2 : kR;      // accumulator groups per thread
     f2_t num2[kP ? kG : 1][W];
-    f2_t den2[kP ? kG : 1][2];                       // even / odd window positions
+    f2_t den2[kP ? kG : 1][2];                       // energy chains (kDenChains used)
     float num1[kP ? 1 : kG][W];
     float den1[kP ? 1 : kG][2];
     int cntv[kR];
@@ -586,7 +590,8 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
                 for (int j = 0; j < W; ++j) {
                     const float v = fmaf(cX[g], F[j + 1] - F[j], F[j]);
                     a.num1[g][j] += v;
-                    a.den1[g][j & 1] = fmaf(v, v, a.den1[g][j & 1]);
+                    a.den1[g][kDenChains == 2 ? (j & 1) : 0] =
+                        fmaf(v, v, a.den1[g][kDenChains == 2 ? (j & 1) : 0]);
                 }
             } else {
                 const int ra = 2 * g, rb = 2 * g + 1;
@@ -609,7 +614,8 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
                                 fmaf(cX[rb], FB[j + 1] - FB[j], FB[j]));
                     }
                     a.num2[g][j] = add2(a.num2[g][j], v);
-                    a.den2[g][j & 1] = fma2(v, v, a.den2[g][j & 1]);
+                    a.den2[g][kDenChains == 2 ? (j & 1) : 0] =
+                        fma2(v, v, a.den2[g][kDenChains == 2 ? (j & 1) : 0]);
                 }
             }
         }
@@ -648,7 +654,7 @@ __device__ __forceinline__ void accum_end(const Accum<W, CFG>& a, int ncand, flo
     for (int r = 0; r < CFG::kR; ++r) {
         const int c = a.cidx[r];
         if (c >= ncand) continue;
-        // the numerator is summed in the same even/odd order as the energy, so a lone
+        // the numerator is summed in the same chain order as the energy, so a lone
         // participating trace gives exactly S = 1
         float nu0 = 0.f, nu1 = 0.f, ac = 0.f, d0, d1;
         #pragma unroll
@@ -661,7 +667,7 @@ __device__ __forceinline__ void accum_end(const Accum<W, CFG>& a, int ncand, flo
             } else {
                 v = a.num1[r][j];
             }
-            if (j & 1) nu1 = fmaf(v, v, nu1); else nu0 = fmaf(v, v, nu0);
+            if (kDenChains == 2 && (j & 1)) nu1 = fmaf(v, v, nu1); else nu0 = fmaf(v, v, nu0);
             ac += v;
         }
         if constexpr (Accum<W, CFG>::kP) {
