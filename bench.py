@@ -93,13 +93,49 @@ def oracle_baseline(ds, C, target_s=15.0, seed=0):
     n = int(min(nrows, max(64, target_s / per_row)))
     rows = np.sort(rng.choice(nrows, n, replace=False))
     t = time.perf_counter()
-    oracle.cmp_semblance(ds, C, w=W, rows=rows, want_cube=False)
+    oracle.cmp_semblance(ds, C, w=W, rows=rows, want_cube=False, nthreads=threads)
     el = time.perf_counter() - t
     inter = n * len(C) * fold
+    # the same oracle on one thread, on a quarter-length sample
+    n1 = int(min(nrows, max(8, target_s / 4 / (per_row * threads))))
+    rows1 = rows[:n1]
+    t = time.perf_counter()
+    oracle.cmp_semblance(ds, C, w=W, rows=rows1, want_cube=False, nthreads=1)
+    el1 = time.perf_counter() - t
+    oracle.cmp_semblance(ds, C, w=W, rows=rows1[:1], want_cube=False, nthreads=threads)
     cores, model = _cpu_info()
     return inter * W / el, dict(cores=threads, cpu=model, seconds=el,
                                 sample=f"{n} seeded output rows of the workload "
-                                       f"(x {len(C)} candidates x fold {fold}), all traces")
+                                       f"(x {len(C)} candidates x fold {fold}), all traces",
+                                single_thread_value=n1 * len(C) * fold * W / el1,
+                                single_thread_sample=f"{n1} of those rows")
+
+
+def crs_oracle_baseline(ds, centrals, A, B, C, target_s=15.0):
+    """Time the FP64 CRS oracle on a deterministic sample: the given central CMPs, every
+    k-th output time (k chosen for about target_s seconds), all candidates.  Returns
+    (trace-samples/s, info)."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    nb = oracle.aperture(ds, centrals, ds["apm"])
+    nrows = int(nb[3][-1])
+    probe = np.arange(0, nrows, max(1, nrows // 8))[:8]
+    t = time.perf_counter()
+    oracle.crs_semblance(ds, nb, A, B, C, w=W, rows=probe, nthreads=threads)
+    per_row = max(time.perf_counter() - t, 1e-4) / len(probe)
+    step = max(1, int(np.ceil(nrows * per_row / target_s)))
+    rows = np.arange(0, nrows, step)
+    t = time.perf_counter()
+    oracle.crs_semblance(ds, nb, A, B, C, w=W, rows=rows, nthreads=threads)
+    el = time.perf_counter() - t
+    owner = np.searchsorted(nb[3], rows, side="right") - 1
+    inter = int(np.sum((nb[0][owner + 1] - nb[0][owner]) * len(A) * len(B) * len(C)))
+    cores, model = _cpu_info()
+    return inter * W / el, dict(cores=threads, cpu=model, seconds=el,
+                                sample=f"{len(centrals)} central CMPs x every {step}th output "
+                                       f"time ({len(rows)} rows) x {len(A) * len(B) * len(C)} "
+                                       "candidates, all aperture traces")
 
 
 class ClockSampler:
@@ -296,7 +332,9 @@ def run_cmp_line(args, torch, dist, seis, synth, rank, world, dev):
         v, info = oracle_baseline(ds, C, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "trace-samples/s", "cores": info["cores"],
                                 "kind": "oracle", "sample": info["sample"],
-                                "cpu": info["cpu"], "seconds": info["seconds"]}
+                                "cpu": info["cpu"], "seconds": info["seconds"],
+                                "single_thread_value": info["single_thread_value"],
+                                "single_thread_sample": info["single_thread_sample"]}
     return line
 
 
@@ -423,6 +461,12 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
     ach = inter * FLOPS_PER_INTERSECTION / (np.mean(kern) / 1e3) / 1e12
     # unique bytes: the traces of every CMP some aperture reaches, read once, plus 6 output
     # values per row; DRAM traffic scaled from the committed capture by the CMPs read
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        host = lambda t: t.cpu().numpy().astype(np.float64)
+        v, info = crs_oracle_baseline(ds, ds["central"][::128][:8], host(A), host(B), host(C),
+                                      target_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": "trace-samples/s", "kind": "oracle", **info}
     tr_ids = ap.nbr_trace[:int(ap.nbr_off[-1])].cpu().numpy()
     cmps = np.unique(np.searchsorted(ds["gather_off"], tr_ids, side="right") - 1)
     cmp_bytes = int(sum(ds["trace_off"][ds["gather_off"][c + 1]] - ds["trace_off"][ds["gather_off"][c]]
@@ -444,7 +488,8 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
                                       "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x "
                                                     f"{SM_MAX_MHZ:g} MHz",
                                       "kernel": f"search_kernel<CRS, w=11, variant {chosen}>",
-                                      "kernel_sources_sha256_16": digest}},
+                                      "kernel_sources_sha256_16": digest},
+                         "cpu_baseline": cpu},
                         clk, args.steps)
 
 
