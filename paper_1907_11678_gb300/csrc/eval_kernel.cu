@@ -22,12 +22,26 @@ constexpr int kEvalWarps = 4;
 constexpr int kEvalThreads = 32 * (kEvalWarps + 1);
 constexpr int kEvalConsumers = 32 * kEvalWarps;
 constexpr int kEvalRows = 32 * kEvalWarps;
+constexpr int kEvalSlots = 2;           // ring depth: four CTAs (20 warps) fit an SM
+constexpr int kEvalCTAs = 4;
+
+// Shared memory of one CTA: the search kernel's slot layout with a two-slot ring.
+struct EvalSmem {
+    float buf[kEvalSlots][kBuf];
+    TraceMeta meta[kEvalSlots][kChunkT];
+    StageDesc desc[kEvalSlots];
+    uint64_t full[kEvalSlots];
+    uint64_t empty[kEvalSlots];
+    float zeros[16];
+    int abort_flag;
+    int pad[3];
+};
 
 template <bool CRS, int W, bool GRAD>
-__global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams P) {
+__global__ void __launch_bounds__(kEvalThreads, kEvalCTAs) eval_kernel(const EvalParams P) {
     constexpr int HW = W / 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SearchSmem& sm = *reinterpret_cast<SearchSmem*>(smem_raw);
+    EvalSmem& sm = *reinterpret_cast<EvalSmem*>(smem_raw);
     const float* smf = reinterpret_cast<const float*>(smem_raw);
 
     const int warp = threadIdx.x >> 5;
@@ -45,7 +59,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
     const float dt = P.dt[owner];
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kSlots; ++s) {
+        for (int s = 0; s < kEvalSlots; ++s) {
             mbar_init(&sm.full[s], 32);
             mbar_init(&sm.empty[s], kEvalConsumers);
         }
@@ -80,9 +94,9 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
         bool done = false;
         int s = 0;
         for (;; ++s) {
-            const int slot = s % kSlots;
-            if (s >= kSlots && !sm.abort_flag) {
-                if (!mbar_wait_backoff(&sm.empty[slot], (uint32_t)(((s / kSlots) & 1) ^ 1))) {
+            const int slot = s % kEvalSlots;
+            if (s >= kEvalSlots && !sm.abort_flag) {
+                if (!mbar_wait_backoff(&sm.empty[slot], (uint32_t)(((s / kEvalSlots) & 1) ^ 1))) {
                     sm.abort_flag = 1;
                     record_status(P.status, kStatusTimeout);
                 }
@@ -107,8 +121,8 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
             mbar_arrive(&sm.full[slot]);
         }
         const int s_end = s;
-        for (int s2 = max(0, s_end - kSlots + 1); s2 <= s_end; ++s2)
-            mbar_wait_bounded(&sm.full[s2 % kSlots], (uint32_t)((s2 / kSlots) & 1));
+        for (int s2 = max(0, s_end - kEvalSlots + 1); s2 <= s_end; ++s2)
+            mbar_wait_bounded(&sm.full[s2 % kEvalSlots], (uint32_t)((s2 / kEvalSlots) & 1));
         return;
     }
 
@@ -134,8 +148,8 @@ __global__ void __launch_bounds__(kEvalThreads, 2) eval_kernel(const EvalParams 
     bool aborted = false;
 
     for (int s = 0;; ++s) {
-        const int slot = s % kSlots;
-        if (!mbar_wait_bounded(&sm.full[slot], (uint32_t)((s / kSlots) & 1))) {
+        const int slot = s % kEvalSlots;
+        if (!mbar_wait_bounded(&sm.full[slot], (uint32_t)((s / kEvalSlots) & 1))) {
             sm.abort_flag = 1;
             record_status(P.status, kStatusTimeout);
             aborted = true;
@@ -332,7 +346,7 @@ __global__ void refine_update_kernel(const RefineParams R) {
 template <bool CRS, int W, bool GRAD>
 static cudaError_t launch_eval_w(const EvalParams& p, cudaStream_t stream) {
     static bool configured[64] = {};
-    const int smem = (int)sizeof(SearchSmem);
+    const int smem = (int)sizeof(EvalSmem);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
