@@ -130,3 +130,36 @@ def test_batch_autotune_picks_a_built_variant_and_keeps_results(seis, small):
     for k in ref:
         np.testing.assert_array_equal(got[k], ref[k])
     seis.autotune_clear()
+
+
+def test_batch_workload_distributions_sampled(seis):
+    """300 items drawn from the batch workload's own distributions (fold 8-120, 1000-4000
+    samples at 2 or 4 ms, 101-201 C or an 11 x 11 x 21 CRS grid); the oracle checks seeded
+    rows of a seeded sample of items of both kinds."""
+    ds, items, A, B, C = synth.batch_workload(n_items=300, seed=41)
+    g = seis.to_device(ds)
+    b = seis.batch_to_device(items, A, B, C, ds["out_rows"])
+    got = _host(seis.batch_semblance(g, b, w=11, mode=0))
+    torch.cuda.synchronize()
+    seis.device_status()
+    rng = np.random.default_rng(42)
+    kinds = set()
+    for idx in rng.choice(len(items), 8, replace=False):
+        it = items[idx]
+        r0, rows = int(it["out_begin"]), int(it["rows"])
+        sub = _item_ds(ds, it)
+        sel = np.sort(rng.choice(rows, min(rows, 12), replace=False))
+        Ci = C[int(it["c_off"]):int(it["c_off"]) + int(it["nC"])]
+        if it["kind"] == 0:
+            ref = oracle.cmp_semblance(sub, Ci, w=11, rows=sel)
+        else:
+            Ai = A[int(it["a_off"]):int(it["a_off"]) + int(it["nA"])]
+            Bi = B[int(it["b_off"]):int(it["b_off"]) + int(it["nB"])]
+            nb = (np.array([0, len(sub["h"])], np.int64), np.arange(len(sub["h"]), dtype=np.int32),
+                  np.float32([it["m_c"]]), np.array([0, rows], np.int64), np.float32([it["dt"]]))
+            ref = oracle.crs_semblance(sub, nb, Ai, Bi, Ci, w=11, rows=sel, want_cube=True)
+        kinds.add(int(it["kind"]))
+        parity.check_picks(got["best_idx"][r0 + sel], got["best_S"][r0 + sel],
+                           got["stack"][r0 + sel], ref, f"batch workload item {idx}",
+                           row_edge=(ref.edge != 0).any(axis=1))
+    assert kinds == {0, 1}

@@ -195,3 +195,34 @@ def test_refine_multi(seis, line, coarse_starts):
     print(f"[parity] refine multi (4 starts): gain over one start {np.mean(Sm - Ss):.4f}, "
           f"|S_gpu - S_oracle| <= 1e-3 on {close.mean():.3f} of rows")
     assert close.mean() >= 0.9
+
+
+def test_refine_workload_sample(seis):
+    """The refinement workload (aperture +-8 CMPs = 816 traces, 2000 samples) on two central
+    CMPs: both sides refine from the oracle's 4 best 7 x 7 x 11 candidates of every row; the
+    oracle's multi-start refinement checks every 40th row."""
+    ds = synth.workload_crs_refine()
+    central = ds["central"][[0, 300]]
+    g = seis.to_device(ds)
+    ap = seis.crs_aperture(g, central, ds["apm"])
+    nb = oracle.aperture(ds, central, ds["apm"])
+    assert int(ap.nbr_off[1] - ap.nbr_off[0]) == 816
+    lo, hi = _ranges()
+    A = np.float32(np.linspace(lo[0], hi[0], 7)); B = np.float32(np.linspace(lo[1], hi[1], 7))
+    C = np.float32(np.linspace(lo[2], hi[2], 11))
+    coarse = oracle.crs_semblance(ds, nb, A, B, C, want_cube=True)
+    starts = oracle.top_starts(coarse.S, A, B, C, 4)
+    st = torch.from_numpy(starts.astype(np.float32)).cuda()
+    multi = seis.crs_refine_multi(g, ap, st, lo, hi, steps=20, step0=0.05, w=11)
+    torch.cuda.synchronize()
+    seis.device_status()
+    Sm = multi["S"].cpu().numpy()
+    S0 = seis.stack(g, ap, st[0], w=11)["S"].cpu().numpy()
+    assert np.all(Sm >= S0 - 1e-6)                 # never below the best coarse start
+    rows = np.arange(0, ap.rows, 40)
+    ref = oracle.crs_refine_multi(ds, nb, starts[:, rows], lo, hi, steps=20, step0=0.05,
+                                  rows=rows)
+    close = np.abs(Sm[rows] - ref.S) <= 1e-3
+    print(f"[parity] refine workload: |S_gpu - S_oracle| <= 1e-3 on {close.mean():.3f} of "
+          f"{len(rows)} rows")
+    assert close.mean() >= 0.9
