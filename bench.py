@@ -328,7 +328,7 @@ def run_cmp_line(args, torch, dist, seis, synth, rank, world, dev):
         "gpu_launches": args.steps,
         "clocks": clk,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle runs at N=1 only
         v, info = oracle_baseline(ds, C, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "trace-samples/s", "cores": info["cores"],
                                 "kind": "oracle", "sample": info["sample"],
@@ -462,7 +462,7 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
     # unique bytes: the traces of every CMP some aperture reaches, read once, plus 6 output
     # values per row; DRAM traffic scaled from the committed capture by the CMPs read
     cpu = None
-    if not args.no_cpu_baseline and rank == 0:
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
         host = lambda t: t.cpu().numpy().astype(np.float64)
         v, info = crs_oracle_baseline(ds, ds["central"][::128][:8], host(A), host(B), host(C),
                                       target_s=args.cpu_seconds)
