@@ -13,7 +13,7 @@
 //   dS = (2 sum_j num_j dnum_j - S N dden) / (N den).
 // Layout: one CTA = one owner x 128 consecutive rows (4 consumer warps, lane = row) plus
 // the producer warp of the search kernel, which stages each trace's window for the union of
-// the CTA's operators through the same bulk-copy ring.
+// the CTA's operators through a two-slot bulk-copy ring (so that four CTAs share an SM).
 #include "search_kernel.cuh"
 
 namespace seis {
