@@ -92,3 +92,24 @@ def test_crs_halo_exchange_matches_single_process(world):
     for rank, ok, t in res:
         assert ok, f"rank {rank} differs from the single-process result"
         assert t == world - 0.5            # max over ranks of rank + 0.5
+
+
+def test_exchange_halos_single_rank_and_zero_halo():
+    """One rank (or no halo) exchanges nothing: the rank's own gathers come back unchanged."""
+    from paper_1907_11678_gb300 import synth
+    ds = synth.crs_line(6, 4, 200, 0.004, 0.0, 500.0, 1, 0, None, seed=12)
+    for world, halo in ((1, 3), (1, 0)):
+        out = sdist.exchange_halos(ds, 6, halo, 0, world)
+        np.testing.assert_array_equal(out["traces"], ds["traces"])
+        np.testing.assert_array_equal(out["trace_off"], ds["trace_off"])
+        np.testing.assert_array_equal(out["gather_off"], ds["gather_off"])
+        np.testing.assert_array_equal(out["h"], ds["h"])
+        np.testing.assert_array_equal(out["m"], ds["m"])
+
+
+def test_exchange_halos_rejects_small_shards():
+    """A rank that owns fewer gathers than the halo cannot serve its neighbours' halos."""
+    from paper_1907_11678_gb300 import synth
+    ds = synth.crs_line(2, 4, 200, 0.004, 0.0, 500.0, 1, 0, None, seed=13)
+    with pytest.raises(ValueError):
+        sdist.exchange_halos(ds, 4, 3, 0, 2)
