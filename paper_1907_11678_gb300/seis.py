@@ -7,6 +7,7 @@ raise; there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 from dataclasses import dataclass, field
@@ -132,6 +133,54 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _input(t, name: str, dev, numel: int | None = None, dtype=torch.float32) -> torch.Tensor:
+    """An input array as a contiguous `dtype` tensor on the gathers' device (no copy when it
+    already is one).  The kernels read `numel` elements through the pointer, so a shorter
+    array is refused here rather than read out of bounds on the GPU."""
+    t = torch.as_tensor(t).to(device=dev, dtype=dtype).contiguous()
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, the call reads {numel}")
+    return t
+
+
+def _output(out: dict, key: str, dev, dtype, numel: int) -> torch.Tensor | None:
+    """A caller-provided output tensor (or None when absent).  The kernels write it in
+    place, so it must already be contiguous, of `dtype`, on the gathers' device and hold at
+    least `numel` elements."""
+    t = out.get(key)
+    if t is None:
+        return None
+    if (not isinstance(t, torch.Tensor) or t.device != dev or t.dtype != dtype
+            or not t.is_contiguous() or t.numel() < numel):
+        raise ValueError(f"out[{key!r}] must be a contiguous {dtype} tensor on {dev} with at "
+                         f"least {numel} elements")
+    return t
+
+
+def _rows_out(dev, rows: int, abc: bool) -> dict:
+    """Fresh best_idx, best_C or best_ABC, best_S and stack outputs for `rows` rows."""
+    out = dict(best_idx=torch.empty(rows, dtype=torch.int32, device=dev))
+    if abc:
+        out["best_ABC"] = torch.empty((rows, 3), dtype=torch.float32, device=dev)
+    else:
+        out["best_C"] = torch.empty(rows, dtype=torch.float32, device=dev)
+    out["best_S"] = torch.empty(rows, dtype=torch.float32, device=dev)
+    out["stack"] = torch.empty(rows, dtype=torch.float32, device=dev)
+    return out
+
+
+def _check_rows_out(out: dict, dev, rows: int, ncand: int, abc: bool) -> None:
+    """Check a caller-provided output dict of a search (see _rows_out; S is [rows, ncand])."""
+    for key in ("best_idx", "best_S", "stack"):
+        if out.get(key) is None:
+            raise ValueError(f"out[{key!r}] is required")
+    _output(out, "best_idx", dev, torch.int32, rows)
+    _output(out, "best_ABC" if abc else "best_C", dev, torch.float32, rows * (3 if abc else 1))
+    _output(out, "best_S", dev, torch.float32, rows)
+    _output(out, "stack", dev, torch.float32, rows)
+    _output(out, "S", dev, torch.float32, rows * ncand)
+
+
 @dataclass
 class Gathers:
     """A set of gathers resident on the GPU (arrays as in include/seis.h)."""
@@ -199,14 +248,14 @@ def cmp_semblance(g: Gathers, C: torch.Tensor, w: int = 11, want_cube: bool = Fa
     best_idx, best_C, best_S, stack (and S [rows, nc] when want_cube)."""
     lib = load_library()
     dev = g.traces.device
+    C = _input(C, "C", dev)
     nc = int(C.numel())
     if out is None:
-        out = dict(best_idx=torch.empty(g.rows, dtype=torch.int32, device=dev),
-                   best_C=torch.empty(g.rows, dtype=torch.float32, device=dev),
-                   best_S=torch.empty(g.rows, dtype=torch.float32, device=dev),
-                   stack=torch.empty(g.rows, dtype=torch.float32, device=dev))
+        out = _rows_out(dev, g.rows, abc=False)
         if want_cube:
             out["S"] = torch.empty((g.rows, nc), dtype=torch.float32, device=dev)
+    else:
+        _check_rows_out(out, dev, g.rows, nc, abc=False)
     rc = lib.cmp_semblance(ctypes.byref(g.descriptor()), _ptr(C), nc, w, _ptr(out.get("S")),
                            _ptr(out["best_idx"]), _ptr(out.get("best_C")), _ptr(out["best_S"]),
                            _ptr(out["stack"]), _stream_handle(stream))
@@ -220,14 +269,14 @@ def cmp_semblance_t0win(g: Gathers, C: torch.Tensor, w: int = 11, want_cube: boo
     cmp_semblance_t0win).  Same outputs as cmp_semblance."""
     lib = load_library()
     dev = g.traces.device
+    C = _input(C, "C", dev)
     nc = int(C.numel())
     if out is None:
-        out = dict(best_idx=torch.empty(g.rows, dtype=torch.int32, device=dev),
-                   best_C=torch.empty(g.rows, dtype=torch.float32, device=dev),
-                   best_S=torch.empty(g.rows, dtype=torch.float32, device=dev),
-                   stack=torch.empty(g.rows, dtype=torch.float32, device=dev))
+        out = _rows_out(dev, g.rows, abc=False)
         if want_cube:
             out["S"] = torch.empty((g.rows, nc), dtype=torch.float32, device=dev)
+    else:
+        _check_rows_out(out, dev, g.rows, nc, abc=False)
     _check(lib.cmp_semblance_t0win(ctypes.byref(g.descriptor()), _ptr(C), nc, w,
                                    _ptr(out.get("S")), _ptr(out["best_idx"]),
                                    _ptr(out.get("best_C")), _ptr(out["best_S"]),
@@ -261,7 +310,9 @@ def crs_aperture(g: Gathers, central, apm: float, hmax: float | None = None,
     seis_crs_aperture_offset when hmax is given: only traces with |h| <= hmax)."""
     lib = load_library()
     dev = g.traces.device
-    central = torch.as_tensor(np.asarray(central, np.int32)).to(dev)
+    if isinstance(central, torch.Tensor):
+        central = central.detach().cpu()
+    central = torch.from_numpy(np.ascontiguousarray(np.asarray(central), np.int32)).to(dev)
     n = int(central.numel())
     nbr_off = torch.empty(n + 1, dtype=torch.int64, device=dev)
     m_c = torch.empty(n, dtype=torch.float32, device=dev)
@@ -289,11 +340,9 @@ def crs_aperture(g: Gathers, central, apm: float, hmax: float | None = None,
 def _crs_search(lib_fn, g, ap, A, B, C, w, want_cube, stream) -> dict:
     lib = load_library()
     dev = g.traces.device
+    A, B, C = _input(A, "A", dev), _input(B, "B", dev), _input(C, "C", dev)
     nA, nB, nC = int(A.numel()), int(B.numel()), int(C.numel())
-    out = dict(best_idx=torch.empty(ap.rows, dtype=torch.int32, device=dev),
-               best_ABC=torch.empty((ap.rows, 3), dtype=torch.float32, device=dev),
-               best_S=torch.empty(ap.rows, dtype=torch.float32, device=dev),
-               stack=torch.empty(ap.rows, dtype=torch.float32, device=dev))
+    out = _rows_out(dev, ap.rows, abc=True)
     if want_cube:
         out["S"] = torch.empty((ap.rows, nA * nB * nC), dtype=torch.float32, device=dev)
     rc = getattr(lib, lib_fn)(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
@@ -339,6 +388,7 @@ def autotune_cmp(g: Gathers, C: torch.Tensor, w: int = 11, reps: int = 2, stream
     (chosen variant, list of mean milliseconds per variant)."""
     lib = load_library()
     dev = g.traces.device
+    C = _input(C, "C", dev)
     bi = torch.empty(g.rows, dtype=torch.int32, device=dev)
     bs = torch.empty(g.rows, dtype=torch.float32, device=dev)
     st = torch.empty(g.rows, dtype=torch.float32, device=dev)
@@ -355,6 +405,7 @@ def autotune_crs(g: Gathers, ap: "Aperture", A, B, C, w: int = 11, reps: int = 2
     """As autotune_cmp for a CRS problem (include/seis.h: seis_autotune_crs)."""
     lib = load_library()
     dev = g.traces.device
+    A, B, C = _input(A, "A", dev), _input(B, "B", dev), _input(C, "C", dev)
     bi = torch.empty(ap.rows, dtype=torch.int32, device=dev)
     bs = torch.empty(ap.rows, dtype=torch.float32, device=dev)
     st = torch.empty(ap.rows, dtype=torch.float32, device=dev)
@@ -387,7 +438,7 @@ def stack(g: Gathers, ap: "Aperture | None", params: torch.Tensor, w: int = 11,
     lib = load_library()
     dev = g.traces.device
     rows = g.rows if ap is None else ap.rows
-    params = params.contiguous()
+    params = _input(params, "params", dev, rows * (1 if ap is None else 3))
     out = dict(stack=torch.empty(rows, dtype=torch.float32, device=dev),
                S=torch.empty(rows, dtype=torch.float32, device=dev),
                N=torch.empty(rows, dtype=torch.int32, device=dev))
@@ -402,7 +453,7 @@ def crs_semblance_grad(g: Gathers, ap: "Aperture", ABC: torch.Tensor, w: int = 1
     """Semblance, dS/d(A,B,C) [rows, 3] and stack at ABC [rows, 3] (adjoint kernel)."""
     lib = load_library()
     dev = g.traces.device
-    ABC = ABC.contiguous()
+    ABC = _input(ABC, "ABC", dev, ap.rows * 3)
     S = torch.empty(ap.rows, dtype=torch.float32, device=dev)
     grad = torch.empty((ap.rows, 3), dtype=torch.float32, device=dev)
     st = torch.empty(ap.rows, dtype=torch.float32, device=dev)
@@ -418,12 +469,12 @@ def crs_refine(g: Gathers, ap: "Aperture", ABC0: torch.Tensor, lo3, hi3, steps: 
     crs_refine).  Returns theta, S, grad, stack (device tensors)."""
     lib = load_library()
     dev = g.traces.device
-    theta = ABC0.detach().clone().contiguous().float()
+    theta = _input(ABC0.detach(), "ABC0", dev, ap.rows * 3).clone()
     S = torch.empty(ap.rows, dtype=torch.float32, device=dev)
     grad = torch.empty((ap.rows, 3), dtype=torch.float32, device=dev)
     st = torch.empty(ap.rows, dtype=torch.float32, device=dev)
     nbytes = lib.seis_refine_workspace_size(ap.rows)
-    if workspace is None or workspace.numel() < nbytes:
+    if workspace is None or workspace.numel() < nbytes + 256:
         workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
     base = workspace.data_ptr()
     aligned = (base + 255) & ~255
@@ -441,10 +492,14 @@ def crs_top_starts(S_cube: torch.Tensor, A: torch.Tensor, B: torch.Tensor, C: to
     """The nstart best coarse candidates of every row of a CRS cube [rows, nA*nB*nC] as
     operators [nstart, rows, 3] (include/seis.h: crs_top_starts)."""
     lib = load_library()
-    S_cube = S_cube.contiguous()
+    dev = S_cube.device
+    A, B, C = _input(A, "A", dev), _input(B, "B", dev), _input(C, "C", dev)
+    if S_cube.dim() != 2 or S_cube.shape[1] != A.numel() * B.numel() * C.numel():
+        raise ValueError(f"S_cube must be [rows, {A.numel() * B.numel() * C.numel()}], "
+                         f"got {tuple(S_cube.shape)}")
+    S_cube = _input(S_cube, "S_cube", dev)
     rows = S_cube.shape[0]
-    A, B, C = (t.contiguous().float() for t in (A, B, C))
-    out = torch.empty((nstart, rows, 3), dtype=torch.float32, device=S_cube.device)
+    out = torch.empty((nstart, rows, 3), dtype=torch.float32, device=dev)
     _check(lib.crs_top_starts(_ptr(S_cube), rows, _ptr(A), A.numel(), _ptr(B), B.numel(),
                               _ptr(C), C.numel(), int(nstart), _ptr(out), _stream_handle(stream)))
     return out
@@ -457,7 +512,9 @@ def crs_refine_multi(g: Gathers, ap: "Aperture", starts: torch.Tensor, lo3, hi3,
     crs_refine_multi).  Returns theta, S, grad, stack (device tensors)."""
     lib = load_library()
     dev = g.traces.device
-    starts = starts.detach().contiguous().float()
+    if starts.dim() != 3 or starts.shape[1:] != (ap.rows, 3):
+        raise ValueError(f"starts must be [nstart, {ap.rows}, 3], got {tuple(starts.shape)}")
+    starts = _input(starts.detach(), "starts", dev)
     theta = torch.empty((ap.rows, 3), dtype=torch.float32, device=dev)
     S = torch.empty(ap.rows, dtype=torch.float32, device=dev)
     grad = torch.empty((ap.rows, 3), dtype=torch.float32, device=dev)
@@ -485,7 +542,7 @@ def crs_pragmatic(g: Gathers, ap_full: "Aperture", ap_cmp: "Aperture", ap_zo: "A
     over the full aperture (include/seis.h: crs_pragmatic).  Returns theta, S, stack."""
     lib = load_library()
     dev = g.traces.device
-    A, B, C = (t.contiguous().float() for t in (A, B, C))
+    A, B, C = _input(A, "A", dev), _input(B, "B", dev), _input(C, "C", dev)
     theta = torch.empty((ap_full.rows, 3), dtype=torch.float32, device=dev)
     S = torch.empty(ap_full.rows, dtype=torch.float32, device=dev)
     st = torch.empty(ap_full.rows, dtype=torch.float32, device=dev)
@@ -555,10 +612,9 @@ def batch_semblance(g: Gathers, b: Batch, w: int = 11, mode: int = 0, stream=Non
     lib = load_library()
     dev = g.traces.device
     if out is None:
-        out = dict(best_idx=torch.empty(b.out_rows, dtype=torch.int32, device=dev),
-                   best_ABC=torch.empty((b.out_rows, 3), dtype=torch.float32, device=dev),
-                   best_S=torch.empty(b.out_rows, dtype=torch.float32, device=dev),
-                   stack=torch.empty(b.out_rows, dtype=torch.float32, device=dev))
+        out = _rows_out(dev, b.out_rows, abc=True)
+    else:
+        _check_rows_out(out, dev, b.out_rows, 0, abc=True)
     base = b.workspace.data_ptr()
     aligned = (base + 255) & ~255
     _check(lib.seis_batch_semblance(
@@ -575,10 +631,7 @@ def autotune_batch(g: Gathers, b: Batch, w: int = 11, reps: int = 1, stream=None
     (include/seis.h: seis_autotune_batch).  Returns (chosen, ms per variant or -1)."""
     lib = load_library()
     dev = g.traces.device
-    out = dict(best_idx=torch.empty(b.out_rows, dtype=torch.int32, device=dev),
-               best_ABC=torch.empty((b.out_rows, 3), dtype=torch.float32, device=dev),
-               best_S=torch.empty(b.out_rows, dtype=torch.float32, device=dev),
-               stack=torch.empty(b.out_rows, dtype=torch.float32, device=dev))
+    out = _rows_out(dev, b.out_rows, abc=True)
     base = b.workspace.data_ptr()
     aligned = (base + 255) & ~255
     nv = lib.seis_search_variant_count()

@@ -150,3 +150,46 @@ def test_pragmatic_and_offset_aperture_arguments(lib):
     assert rc == -1 and "aperture" in _err(lib)
     lib.seis_pragmatic_workspace_size.restype = ctypes.c_size_t
     assert lib.seis_pragmatic_workspace_size(i64(100)) >= 100 * 52
+
+
+# --- the binding refuses malformed arrays on the host, before any kernel could read them ----
+
+@pytest.fixture(scope="module")
+def host_gathers(lib):
+    import torch
+    from paper_1907_11678_gb300 import seis, synth
+    ds = synth.crs_line(6, 4, 200, 0.004, 0.0, 500.0, 1, 0, None, seed=21)
+    return seis, torch, seis.to_device(ds, device="cpu")
+
+
+def test_binding_refuses_short_operator_arrays(host_gathers):
+    seis, torch, g = host_gathers
+    with pytest.raises(ValueError, match="params"):
+        seis.stack(g, None, torch.zeros(g.rows - 1))
+
+
+def test_binding_refuses_wrong_output_arrays(host_gathers):
+    seis, torch, g = host_gathers
+    C = torch.ones(5)
+    good = dict(best_idx=torch.zeros(g.rows, dtype=torch.int32),
+                best_S=torch.zeros(g.rows), stack=torch.zeros(g.rows))
+    for key, bad in (("best_idx", torch.zeros(g.rows)),                       # dtype
+                     ("best_S", torch.zeros(g.rows - 1)),                     # size
+                     ("stack", torch.zeros(2 * g.rows)[::2]),                 # layout
+                     ("S", torch.zeros(g.rows, 4))):                          # cube size
+        out = dict(good, **{key: bad})
+        with pytest.raises(ValueError, match=key):
+            seis.cmp_semblance(g, C, out=out)
+    with pytest.raises(ValueError, match="required"):
+        seis.cmp_semblance(g, C, out={"best_idx": good["best_idx"]})
+
+
+def test_binding_refuses_mis_shaped_cube_and_starts(host_gathers):
+    seis, torch, g = host_gathers
+    A, B, C = torch.zeros(3), torch.zeros(2), torch.zeros(4)
+    with pytest.raises(ValueError, match="S_cube"):
+        seis.crs_top_starts(torch.zeros(10, 23), A, B, C, 2)
+    ap = seis.Aperture(*(torch.zeros(1),) * 5, n_central=1, max_rows=200, rows=200)
+    with pytest.raises(ValueError, match="starts"):
+        seis.crs_refine_multi(g, ap, torch.zeros(2, 199, 3), (0, 0, 0), (1, 1, 1))
+
