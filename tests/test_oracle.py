@@ -86,6 +86,77 @@ def test_random_bounds_cauchy_schwarz():
     assert np.all(r.best_S >= r.second_S)
 
 
+
+# --- symmetries of Eq. 1: the order of the traces and the scale of the amplitudes -------
+
+def _permute_within_gathers(ds, seed):
+    """The same gathers, each gather's traces (with their offsets and midpoints) in a
+    random order."""
+    rng = np.random.default_rng(seed)
+    go, to = ds["gather_off"], ds["trace_off"]
+    order = np.concatenate([go[g] + rng.permutation(go[g + 1] - go[g])
+                            for g in range(len(go) - 1)]).astype(np.int64)
+    pieces = [ds["traces"][to[i]:to[i + 1]] for i in order]
+    off = np.zeros(len(order) + 1, np.int64)
+    off[1:] = np.cumsum([len(a) for a in pieces])
+    out = dict(ds, traces=np.concatenate(pieces), trace_off=off, h=ds["h"][order])
+    if ds.get("m") is not None:
+        out["m"] = ds["m"][order]
+    return out
+
+
+def _assert_same_search(a, b, atol=1e-12):
+    np.testing.assert_array_equal(b.N, a.N)
+    np.testing.assert_allclose(b.S, a.S, rtol=0, atol=atol)
+    np.testing.assert_allclose(b.stack, a.stack, rtol=0, atol=atol)
+    clear = a.best_S - a.second_S > 1e-9
+    assert clear.mean() > 0.9
+    np.testing.assert_array_equal(b.best_idx[clear], a.best_idx[clear])
+
+
+def test_cmp_trace_order_invariance():
+    """Eq. 1 sums over the traces of a gather, so their order changes S, the trace count,
+    the pick and the stack by rounding only (a trace paired with another trace's offset, or
+    a sum that leaves its gather, would not)."""
+    ds = synth.cmp_line(3, 13, 400, 0.004, 0.0, 1800.0, 3, 1.0, seed=31)
+    C = _grid(23)
+    _assert_same_search(oracle.cmp_semblance(ds, C),
+                        oracle.cmp_semblance(_permute_within_gathers(ds, 32), C))
+
+
+def test_crs_aperture_order_invariance():
+    """The CRS sums run over the aperture's traces: listing them in another order (and
+    reordering the traces of every CMP in the line) changes nothing beyond rounding."""
+    ds = synth.crs_line(9, 8, 300, 0.004, 0.0, 1200.0, 2, 1, 2.0, seed=33)
+    A = np.float32([-3e-4, 0.0, 2e-4]); B = np.float32([-1e-6, 0.0, 1e-6])
+    C = np.float32(_grid(5))
+    central = [3, 4, 5]
+    nb = oracle.aperture(ds, central, 37.5)
+    a = oracle.crs_semblance(ds, nb, A, B, C, want_cube=True)
+    rng = np.random.default_rng(34)
+    off, tr = nb[0], nb[1].copy()
+    for i in range(len(central)):
+        tr[off[i]:off[i + 1]] = rng.permutation(tr[off[i]:off[i + 1]])
+    b = oracle.crs_semblance(ds, (off, tr) + tuple(nb[2:]), A, B, C, want_cube=True)
+    _assert_same_search(a, b)
+    p = _permute_within_gathers(ds, 35)
+    _assert_same_search(a, oracle.crs_semblance(p, oracle.aperture(p, central, 37.5),
+                                                A, B, C, want_cube=True))
+
+
+def test_amplitude_scale_is_exact():
+    """S is a ratio of two quadratic forms in the amplitudes and the stack is linear in
+    them: scaling every trace by -4 (a power of two, so every FP64 step scales exactly)
+    leaves S and the pick bit-identical and scales the stack by exactly -4."""
+    ds = synth.cmp_line(2, 11, 300, 0.004, 0.0, 1500.0, 3, 2.0, seed=36)
+    C = _grid(17)
+    a = oracle.cmp_semblance(ds, C)
+    b = oracle.cmp_semblance(dict(ds, traces=np.float32(-4.0) * ds["traces"]), C)
+    np.testing.assert_array_equal(b.S, a.S)
+    np.testing.assert_array_equal(b.best_idx, a.best_idx)
+    np.testing.assert_array_equal(b.stack, -4.0 * a.stack)
+
+
 # --- an exactly sampled hyperbolic event: S = 1 at the true C, argmax = true C ---------
 
 def _exact_hyperbola(n0=240, ns=700, hw=5):
