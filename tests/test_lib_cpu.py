@@ -193,3 +193,25 @@ def test_binding_refuses_mis_shaped_cube_and_starts(host_gathers):
     with pytest.raises(ValueError, match="starts"):
         seis.crs_refine_multi(g, ap, torch.zeros(2, 199, 3), (0, 0, 0), (1, 1, 1))
 
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """With libseis.so absent the binding raises on the first call: there is no CPU
+    fallback to take its place."""
+    import subprocess
+    import sys
+    code = (
+        "from paper_1907_11678_gb300 import build, seis, synth\n"
+        f"build.LIB = {str(tmp_path / 'libseis.so')!r}\n"
+        "ds = synth.crs_line(3, 4, 200, 0.004, 0.0, 500.0, 1, 0, None, seed=22)\n"
+        "g = seis.to_device(ds, device='cpu')\n"
+        "try:\n"
+        "    seis.cmp_semblance(g, seis.velocity_grid(1400.0, 4500.0, 5, device='cpu'))\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+        "else:\n"
+        "    print('no error')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "raised: libseis.so not found" in r.stdout
