@@ -3,7 +3,8 @@ semblance search:
   - semblance: |dS| <= 1e-4 absolute, except (row, candidate) entries the oracle flags as
     a mask edge on an interpolation knot (reading c5), which must stay below 0.01 %;
   - picked candidates identical, except where the oracle's top-two gap is below 1e-4 or
-    the row holds a flagged entry;
+    the oracle's or the GPU's pick is a flagged entry (a flagged entry elsewhere in the row
+    cannot move the pick: if neither pick is flagged, both S values are within tolerance);
   - stacked traces: relative L2 error <= 1e-4 over rows whose picks agree.
 """
 import numpy as np
@@ -30,7 +31,9 @@ def check_cube(S_gpu, ref, label="", max_exempt=MAX_EXEMPT_SMALL):
     return rep
 
 
-def check_picks(best_idx, best_S, stack, ref, label="", row_edge=None):
+def check_picks(best_idx, best_S, stack, ref, label="", row_edge=None, edge=None):
+    """row_edge [rows]: waive whole rows; edge [rows, ncand] (the oracle's flags): waive a
+    row only where the oracle's or the GPU's pick is flagged."""
     best_idx = np.asarray(best_idx)
     best_S = np.asarray(best_S, np.float64)
     stack = np.asarray(stack, np.float64)
@@ -38,6 +41,11 @@ def check_picks(best_idx, best_S, stack, ref, label="", row_edge=None):
     ok_rows = gap >= GAP_TOL
     if row_edge is not None:
         ok_rows &= ~row_edge
+    if edge is not None:
+        e = np.asarray(edge) != 0
+        r = np.arange(len(best_idx))
+        gpu_pick = np.clip(best_idx, 0, e.shape[1] - 1)
+        ok_rows &= ~(e[r, ref.best_idx] | e[r, gpu_pick])
     same = best_idx == ref.best_idx
     bad = ok_rows & ~same
     assert not bad.any(), (f"{label}: {bad.sum()} picks differ, e.g. rows {np.nonzero(bad)[0][:5]}"

@@ -36,9 +36,8 @@ def _check_all(seis, ds, C, w=11, label="", max_exempt=parity.MAX_EXEMPT_SMALL):
     got = _run(seis, ds, C, w)
     ref = oracle.cmp_semblance(ds, C, w=w)
     rep = parity.check_cube(got["S"], ref, label, max_exempt=max_exempt)
-    row_edge = (ref.edge != 0).any(axis=1)
     rep.update(parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, label,
-                                  row_edge=row_edge))
+                                  edge=ref.edge))
     np.testing.assert_array_equal(got["best_C"], C[got["best_idx"]])
     return got, ref, rep
 
@@ -127,9 +126,8 @@ def test_cmp_line_full_size_sampled(seis):
     rows = np.concatenate([rows, [0, 1999, 2000, 8191999]])
     ref = oracle.cmp_semblance(ds, C, rows=rows)
     sub = {k: got[k][rows] for k in ("best_idx", "best_S", "stack")}
-    row_edge = (ref.edge != 0).any(axis=1)
     rep = parity.check_picks(sub["best_idx"], sub["best_S"], sub["stack"], ref, "cmp-line",
-                             row_edge=row_edge)
+                             edge=ref.edge)
     assert rep["pick_agree"] > 0.98
     assert np.all(got["best_S"] >= 0) and np.all(got["best_S"] <= 1.0 + 1e-5)
 
@@ -158,7 +156,7 @@ def _check_t0win(seis, ds, C, w, label, max_exempt=parity.MAX_EXEMPT_SMALL):
     ref = oracle.cmp_semblance(ds, C, w=w, t0_window=True)
     parity.check_cube(got["S"], ref, label, max_exempt=max_exempt)
     rep = parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, label,
-                             row_edge=(ref.edge != 0).any(axis=1))
+                             edge=ref.edge)
     np.testing.assert_array_equal(got["best_C"], C[got["best_idx"]])
     return rep
 

@@ -72,9 +72,8 @@ def test_crs_small_full_cube(seis):
     got = _run(seis, g, ap, A, B, C)
     ref = oracle.crs_semblance(ds, nb, A, B, C, want_cube=True)
     parity.check_cube(got["S"], ref, "crs-small")
-    row_edge = (ref.edge != 0).any(axis=1)
     parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, "crs-small",
-                       row_edge=row_edge)
+                       edge=ref.edge)
     ia, rem = np.divmod(got["best_idx"], 3 * 7)
     ib, ic = np.divmod(rem, 7)
     np.testing.assert_array_equal(got["best_ABC"], np.stack([A[ia], B[ib], C[ic]], 1))
@@ -92,7 +91,7 @@ def test_crs_windows_and_ragged(seis, w):
     ref = oracle.crs_semblance(ds, nb, A, B, C, w=w, want_cube=True)
     parity.check_cube(got["S"], ref, f"crs-w{w}")
     parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, f"crs-w{w}",
-                       row_edge=(ref.edge != 0).any(axis=1))
+                       edge=ref.edge)
 
 
 def test_crs_exact_dipping_plane(seis):
@@ -149,7 +148,7 @@ def test_crs_workload_slice_full_grid(seis):
     rows = np.sort(rng.choice(ap.rows, 24, replace=False))
     ref = oracle.crs_semblance(ds, nb, A, B, C, rows=rows, want_cube=True)
     rep = parity.check_picks(got["best_idx"][rows], got["best_S"][rows], got["stack"][rows],
-                             ref, "crs-line", row_edge=(ref.edge != 0).any(axis=1))
+                             ref, "crs-line", edge=ref.edge)
     assert rep["pick_agree"] >= 0.9
 
 
@@ -167,7 +166,7 @@ def test_crs_paper_table1_shapes(seis, shape):
     ref = oracle.crs_semblance(ds, nb, A, B, C, want_cube=True)
     parity.check_cube(got["S"], ref, f"crs {shape}")
     parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, f"crs {shape}",
-                       row_edge=(ref.edge != 0).any(axis=1))
+                       edge=ref.edge)
 
 
 def test_crs_pragmatic_matches_oracle(seis):
@@ -216,7 +215,7 @@ def test_crs_t0win_matches_oracle(seis, w):
     ref = oracle.crs_semblance(ds, nb, A, B, C, w=w, want_cube=True, t0_window=True)
     parity.check_cube(got["S"], ref, f"crs t0win w{w}", max_exempt=w * parity.MAX_EXEMPT_SMALL)
     parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, f"crs t0win w{w}",
-                       row_edge=(ref.edge != 0).any(axis=1))
+                       edge=ref.edge)
     ia, rem = np.divmod(got["best_idx"], 3 * 7)
     ib, ic = np.divmod(rem, 7)
     np.testing.assert_array_equal(got["best_ABC"], np.stack([A[ia], B[ib], C[ic]], 1))
