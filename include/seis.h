@@ -15,8 +15,14 @@
  *     central CDP (CRS); rows of owner g are out_off[g] .. out_off[g+1]-1.
  *   - Return codes: SEIS_OK (0) or a negative error; nothing aborts, throws or prints.
  *     seis_last_error() returns a thread-local message for the last failure.
- *   - Kernels never read or write outside the arrays described here, whatever the
- *     contents of the offset arrays; inconsistent offsets give unspecified results.
+ *   - The offset and index arrays (trace_off, gather_off, out_off, nbr_off, nbr_trace)
+ *     live in device memory and are not validated: they must be non-decreasing, index
+ *     inside the arrays they describe, and agree with the host-side counts passed beside
+ *     them (ngathers, ntraces, max_rows, n_central, and the `rows` of crs_refine,
+ *     crs_refine_multi and crs_pragmatic).  The kernels index through them, so offsets
+ *     that break these rules can make a kernel read or write outside the caller's
+ *     arrays.  Host-side sizes and pointers are checked on every call, and the batch
+ *     entry point range-checks each item on the device (see seis_batch_item).
  *   - A device wait that does not finish within about 2 s (a bulk copy that never
  *     lands) makes the kernel record SEIS_ETIMEOUT in the device status word and
  *     return; seis_device_status() reports and clears it.
