@@ -209,8 +209,28 @@ class Gathers:
         return self._desc
 
 
+def _check_dataset(traces, trace_off, h, m, gather_off, out_off, dt) -> None:
+    """The offset arrays are the kernels' only bounds (include/seis.h), so a dataset whose
+    offsets do not index inside its own arrays is refused here, on the host."""
+    def monotone(name, a, lo, hi):
+        if len(a) < 1 or a[0] < lo or a[-1] > hi or np.any(np.diff(a) < 0):
+            raise ValueError(f"{name} must be non-decreasing within [{lo}, {hi}]")
+    ntr = len(trace_off) - 1
+    G = len(gather_off) - 1
+    monotone("trace_off", trace_off, 0, len(traces))
+    monotone("gather_off", gather_off, 0, ntr)
+    if len(out_off) != G + 1:
+        raise ValueError(f"out_off needs {G + 1} entries (one per gather, plus one)")
+    monotone("out_off", out_off, 0, np.iinfo(np.int64).max)
+    if len(h) != ntr or (m is not None and len(m) != ntr):
+        raise ValueError(f"h (and m) need one entry per trace ({ntr})")
+    if len(dt) != G:
+        raise ValueError(f"dt needs one entry per gather ({G})")
+
+
 def to_device(ds: dict, device="cuda", non_blocking=False) -> Gathers:
-    """Copy a dataset dict (numpy arrays, see synth.py) to the GPU."""
+    """Copy a dataset dict (numpy arrays, see synth.py) to the GPU, after checking that its
+    offsets index inside its arrays."""
     def t(a, dt):
         x = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
         if non_blocking:
@@ -219,6 +239,9 @@ def to_device(ds: dict, device="cuda", non_blocking=False) -> Gathers:
     trace_off = np.asarray(ds["trace_off"], np.int64)
     out_off = np.asarray(ds["out_off"], np.int64)
     gather_off = np.asarray(ds["gather_off"], np.int64)
+    _check_dataset(np.ravel(ds["traces"]), trace_off, np.ravel(ds["h"]),
+                   None if ds.get("m") is None else np.ravel(ds["m"]), gather_off, out_off,
+                   np.ravel(ds["dt"]))
     return Gathers(traces=t(ds["traces"], np.float32), trace_off=t(trace_off, np.int64),
                    h=t(ds["h"], np.float32),
                    m=t(ds["m"], np.float32) if ds.get("m") is not None else None,

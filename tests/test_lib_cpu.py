@@ -215,3 +215,23 @@ def test_missing_library_fails_loudly(tmp_path):
                        timeout=300)
     assert r.returncode == 0, r.stderr
     assert "raised: libseis.so not found" in r.stdout
+
+
+def test_binding_refuses_inconsistent_offsets(host_gathers):
+    """The kernels index through the offset arrays, so to_device refuses offsets that do not
+    index inside the dataset's own arrays."""
+    seis, torch, _ = host_gathers
+    from paper_1907_11678_gb300 import synth
+    ds = synth.crs_line(4, 4, 200, 0.004, 0.0, 500.0, 1, 0, None, seed=23)
+    seis.to_device(ds, device="cpu")                                   # consistent: accepted
+    bad = []
+    t = ds["trace_off"].copy(); t[-1] += 1; bad.append(("trace_off", dict(ds, trace_off=t)))
+    t = ds["trace_off"].copy(); t[2], t[3] = t[3], t[2]; bad.append(("trace_off", dict(ds, trace_off=t)))
+    g = ds["gather_off"].copy(); g[-1] += 1; bad.append(("gather_off", dict(ds, gather_off=g)))
+    o = ds["out_off"].copy(); o[1] = -1; bad.append(("out_off", dict(ds, out_off=o)))
+    bad.append(("out_off", dict(ds, out_off=ds["out_off"][:-1])))
+    bad.append(("h", dict(ds, h=ds["h"][:-1])))
+    bad.append(("dt", dict(ds, dt=ds["dt"][:-1])))
+    for name, d in bad:
+        with pytest.raises(ValueError, match=name):
+            seis.to_device(d, device="cpu")
