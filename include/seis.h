@@ -107,7 +107,7 @@ int seis_selftest_wait_timeout(int32_t limit_us, void* stream);
  * hybrid FP32 accumulation); every variant computes bit-identical results.  A launch uses
  * the variant the autotuner recorded for its shape bucket (kind, w, and log2 buckets of
  * the candidate count, rows per owner and traces per gather), else the process-wide
- * default set here (initially 5).  Changing it while other host threads launch searches is
+ * default set here (initially 4).  Changing it while other host threads launch searches is
  * allowed; those launches use either value. */
 int seis_search_variant_count(void);
 const char* seis_search_variant_name(int variant);      /* "" if out of range */

@@ -113,10 +113,13 @@ def test_autotune_cache_roundtrip(lib, tmp_path):
 
 def test_variant_selector(lib):
     n = lib.seis_search_variant_count()
-    assert n >= 2
+    assert n >= 5
+    default = lib.seis_get_search_variant()
+    assert default == 4                          # the packed 15 x 2 shape until changed
     assert lib.seis_set_search_variant(n) == -1
+    assert lib.seis_set_search_variant(-1) == -1
     assert lib.seis_set_search_variant(0) == 0 and lib.seis_get_search_variant() == 0
-    assert lib.seis_set_search_variant(5) == 0
+    assert lib.seis_set_search_variant(default) == 0
 
 
 def test_refine_starts_arguments_are_checked(lib):
