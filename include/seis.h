@@ -347,10 +347,12 @@ int seis_autotune_batch(const seis_gathers* d, const seis_batch_item* items, int
  * its persistent mode (mode 0) with the scratch (work counter and task table) kept in a
  * device array inside the library instead of a caller workspace.  Limits and behaviour:
  *   - at most SEIS_NOALLOC_MAX_ITEMS items per call (SEIS_EINVAL beyond); the array,
- *     256 + 8 * (SEIS_NOALLOC_MAX_ITEMS + 1) bytes (about 512 KiB), is held on every GPU
- *     that loads the library until the process exits;
+ *     seis_batch_workspace_size(SEIS_NOALLOC_MAX_ITEMS) = 524,800 bytes (about 512 KiB),
+ *     is held on every GPU that loads the library until the process exits;
  *   - the first call on a device looks the array's device address up (a runtime query,
- *     not an allocation), so make that first call before any stream capture;
+ *     not an allocation) and keeps it, so make that first call before any stream capture,
+ *     and do not call this entry point on a device after cudaDeviceReset() in the same
+ *     process (the kept address belongs to the context the reset destroyed);
  *   - every call shares the array (each rebuilds the task table and zeroes the counter):
  *     calls whose work overlaps on the GPU race on it, so serialise them;
  *   - nothing is allocated: no cudaMalloc, no cudaFree, no allocating library routine.

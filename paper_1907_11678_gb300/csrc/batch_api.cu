@@ -5,6 +5,7 @@
 #include <vector>
 #include "seis.h"
 #include "seis_internal.h"
+#include "batch_scratch.h"
 #include "seis_dev.cuh"
 
 namespace seis {
@@ -89,15 +90,12 @@ cudaError_t launch_batch_setup(const BatchParams& p, int64_t out_rows, cudaStrea
     return cudaGetLastError();
 }
 
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
 }  // namespace seis
 
 using namespace seis;
 
 extern "C" size_t seis_batch_workspace_size(int64_t nitems) {
-    if (nitems < 0) return 0;
-    return 256 + align256(((size_t)nitems + 1) * sizeof(int64_t));
+    return batch_workspace_bytes(nitems);
 }
 
 namespace seis {

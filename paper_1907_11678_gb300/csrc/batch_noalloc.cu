@@ -15,14 +15,21 @@
 #include <cuda_runtime.h>
 #include "seis.h"
 #include "seis_internal.h"
+#include "batch_scratch.h"
 
 namespace seis {
 
-// [0, 256): the work counter; [256, ...): the task table (SEIS_NOALLOC_MAX_ITEMS + 1 int64)
-static constexpr size_t kNoallocBytes = 256 + ((size_t)SEIS_NOALLOC_MAX_ITEMS + 1) * sizeof(int64_t);
+// [0, 256): the work counter; [256, ...): the task table (SEIS_NOALLOC_MAX_ITEMS + 1 int64,
+// rounded up to 256 bytes) -- exactly what seis_batch_workspace_size(SEIS_NOALLOC_MAX_ITEMS)
+// asks of a caller workspace, so a call with the maximum item count passes its check.
+static constexpr size_t kNoallocBytes = batch_workspace_bytes(SEIS_NOALLOC_MAX_ITEMS);
+static_assert(kNoallocBytes == 256 + 8 * ((size_t)SEIS_NOALLOC_MAX_ITEMS + 1) + 248,
+              "the array holds the counter and the 256-byte-rounded task table of the maximum "
+              "item count");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-// The array's device address, looked up once per device with that device current.
+// The array's device address, looked up once per device with that device current.  It stays
+// valid for the life of the device's primary context (a cudaDeviceReset ends it).
 static void* g_noalloc_addr[64] = {};
 
 static int noalloc_scratch(void** out) {

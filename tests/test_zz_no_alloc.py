@@ -55,6 +55,62 @@ def test_noalloc_matches_workspace_entry_point_twice():
             np.testing.assert_array_equal(out[k].cpu().numpy(), ref[k], err_msg=f"call {call}: {k}")
 
 
+def _noalloc_fn(lib):
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.seis_batch_semblance_noalloc.restype = ctypes.c_int
+    lib.seis_batch_semblance_noalloc.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32,
+                                                 vp, vp, vp, vp, i64, vp]
+    return lib.seis_batch_semblance_noalloc
+
+
+def test_noalloc_takes_its_documented_maximum():
+    """Exactly SEIS_NOALLOC_MAX_ITEMS tiny items (fold 1, 40 samples, 8 output rows, three C
+    candidates each) are accepted and give the workspace entry point's results bit for bit."""
+    from paper_1907_11678_gb300 import build, seis
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    lib = seis.load_library()
+    fn = _noalloc_fn(lib)
+    n, L, rows = 65536, 40, 8
+    rng = np.random.default_rng(29)
+    traces = rng.standard_normal(n * L).astype(np.float32)
+    ds = dict(traces=traces, trace_off=np.arange(n + 1, dtype=np.int64) * L,
+              h=rng.uniform(0.0, 60.0, n).astype(np.float32), m=np.zeros(n, np.float32),
+              gather_off=np.array([0, n], np.int64), out_off=np.array([0, n * rows], np.int64),
+              dt=np.float32([0.004]))
+    items = np.zeros(n, synth.BATCH_ITEM_DTYPE)
+    items["trace_begin"] = np.arange(n)
+    items["trace_end"] = np.arange(n) + 1
+    items["out_begin"] = np.arange(n) * rows
+    items["rows"] = rows
+    items["dt"] = 0.004
+    items["nA"] = items["nB"] = 1
+    items["nC"] = 3
+    poolA = np.zeros(1, np.float32)
+    poolB = np.zeros(1, np.float32)
+    poolC = np.float32(4.0 / np.array([1500.0, 2500.0, 4000.0]) ** 2)
+    g = seis.to_device(ds)
+    b = seis.batch_to_device(items, poolA, poolB, poolC, n * rows)
+    assert lib.seis_batch_workspace_size(n) == 524800
+    ref = {k: v.cpu().numpy() for k, v in seis.batch_semblance(g, b, w=3, mode=0).items()}
+    torch.cuda.synchronize()
+    seis.device_status()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    out = dict(best_idx=torch.full((n * rows,), -7, dtype=torch.int32, device="cuda"),
+               best_ABC=torch.full((n * rows, 3), -7.0, device="cuda"),
+               best_S=torch.full((n * rows,), -7.0, device="cuda"),
+               stack=torch.full((n * rows,), -7.0, device="cuda"))
+    rc = fn(ctypes.byref(g.descriptor()), P(b.items), n, P(b.poolA), 1, P(b.poolB), 1,
+            P(b.poolC), 3, 3, P(out["best_idx"]), P(out["best_ABC"]), P(out["best_S"]),
+            P(out["stack"]), n * rows, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, lib.seis_last_error().decode()
+    torch.cuda.synchronize()
+    seis.device_status()
+    for k in ref:
+        np.testing.assert_array_equal(out[k].cpu().numpy(), ref[k], err_msg=k)
+    assert (ref["best_S"] > 0).mean() > 0.5          # the rows were really searched
+
+
 def test_noalloc_rejects_too_many_items():
     from paper_1907_11678_gb300 import seis
     lib = seis.load_library()
