@@ -11,11 +11,16 @@ a single trace, zero data, Cauchy-Schwarz bounds), an exactly-sampled hyperbolic
 event and an exactly-sampled dipping plane (S = 1 at the true operator), a
 hand-derived worked example under tests/golden/, a pure-Python brute force on tiny
 inputs, numpy.interp for the stack of a single trace, the CRS -> CMP reductions and
-central finite differences of the gradient.  The refinement (reading c16) is pinned
-only by its invariants (monotone S, bounds respected, the exact operator of a sampled
-plane reached from a nearby start, the best of several starts never below any one of
-them), so its result is "parity unpinned" beyond them.  The start selection
-(top_starts) is pinned by hand-worked rows with ties.
+central finite differences of the gradient.  The refinement (reading c16): its BFGS
+update by the secant condition, symmetry, positive definiteness, the direct (Hessian)
+form of the same update and the quadratic-termination property; its trajectory by a
+hand-worked two-step case (with the C axis alone active, the second step is the secant
+step of one-dimensional BFGS) and by its invariants (monotone S, bounds respected, the
+exact operator of a sampled plane reached from a nearby start, the best of several
+starts never below any one of them).  The start selection (top_starts) is pinned by
+hand-worked rows with ties.  The admissible ranges of S, stack and N where FP32 rounding
+may decide a trace's participation either way (reading c5) are pinned by brute force
+over the flagged traces in and out.
 """
 from __future__ import annotations
 
@@ -102,6 +107,25 @@ class Result(dict):
     __getattr__ = dict.__getitem__
 
 
+class _Ranges(ctypes.Structure):
+    """oracle_ranges of seis_oracle.c: per entry, the admissible range of S, the stack and N
+    over the outcomes FP32 rounding may give the flagged traces (reading c5), and the stack
+    at the entry."""
+    _fields_ = [("S_lo", _vp), ("S_hi", _vp), ("stack", _vp), ("st_lo", _vp), ("st_hi", _vp),
+                ("N_lo", _vp), ("N_hi", _vp)]
+
+
+def _ranges(shape):
+    """Output arrays of the admissible ranges and the ctypes structure pointing at them."""
+    arr = dict(S_lo=np.empty(shape, np.float64), S_hi=np.empty(shape, np.float64),
+               stack_at=np.empty(shape, np.float64), st_lo=np.empty(shape, np.float64),
+               st_hi=np.empty(shape, np.float64), N_lo=np.empty(shape, np.int32),
+               N_hi=np.empty(shape, np.int32))
+    st = _Ranges(_p(arr["S_lo"]), _p(arr["S_hi"]), _p(arr["stack_at"]), _p(arr["st_lo"]),
+                 _p(arr["st_hi"]), _p(arr["N_lo"]), _p(arr["N_hi"]))
+    return arr, st
+
+
 def cmp_semblance(ds, C, w=11, rows=None, want_cube=True, knot_eps=1e-3, nthreads=0,
                   t0_window=False) -> Result:
     """CMP search (Eq. 1, Algorithm 1, Section 3.2) on dataset ``ds`` (dict of arrays:
@@ -124,6 +148,7 @@ def cmp_semblance(ds, C, w=11, rows=None, want_cube=True, knot_eps=1e-3, nthread
     S = np.empty((nrows, nc), np.float64) if want_cube else None
     N = np.empty((nrows, nc), np.int32) if want_cube else None
     edge = np.empty((nrows, nc), np.int8) if want_cube else None
+    rng, rst = _ranges((nrows, nc)) if want_cube else ({}, None)
     bi = np.empty(nrows, np.int32)
     bs = np.empty(nrows, np.float64)
     b2 = np.empty(nrows, np.float64)
@@ -133,10 +158,11 @@ def cmp_semblance(ds, C, w=11, rows=None, want_cube=True, knot_eps=1e-3, nthread
             _p(dt), ctypes.c_int64(G), _p(C), ctypes.c_int32(nc),
             ctypes.c_int32(w), _p(rows_a), ctypes.c_int64(nrows),
             _p(S), _p(N), _p(edge), _p(bi), _p(bs), _p(b2), _p(st),
-            ctypes.c_double(knot_eps), ctypes.c_int32(nthreads))
+            ctypes.c_double(knot_eps), ctypes.c_int32(nthreads),
+            None if rst is None else ctypes.byref(rst))
     if rc != 0:
         raise ValueError("seis_oracle_cmp: invalid arguments")
-    return Result(S=S, N=N, edge=edge, best_idx=bi, best_S=bs, second_S=b2, stack=st)
+    return Result(S=S, N=N, edge=edge, best_idx=bi, best_S=bs, second_S=b2, stack=st, **rng)
 
 
 def neighbours(ds, central, apm):
@@ -193,20 +219,22 @@ def crs_semblance(ds, nb, A, B, C, w=11, rows=None, want_cube=False, knot_eps=1e
     S = np.empty((nrows, ncand), np.float64) if want_cube else None
     N = np.empty((nrows, ncand), np.int32) if want_cube else None
     edge = np.empty((nrows, ncand), np.int8) if want_cube else None
+    rng, rst = _ranges((nrows, ncand)) if want_cube else ({}, None)
     bi = np.empty(nrows, np.int32)
     bs = np.empty(nrows, np.float64)
     b2 = np.empty(nrows, np.float64)
     st = np.empty(nrows, np.float64)
     fn = lib.seis_oracle_crs_t0win if t0_window else lib.seis_oracle_crs
     rc = fn(*[_p(a) for a in arrs], ctypes.c_int64(ncen),
-                             _p(A), ctypes.c_int32(len(A)), _p(B), ctypes.c_int32(len(B)),
-                             _p(C), ctypes.c_int32(len(C)), ctypes.c_int32(w),
-                             _p(rows_a), ctypes.c_int64(nrows),
-                             _p(S), _p(N), _p(edge), _p(bi), _p(bs), _p(b2), _p(st),
-                             ctypes.c_double(knot_eps), ctypes.c_int32(nthreads))
+            _p(A), ctypes.c_int32(len(A)), _p(B), ctypes.c_int32(len(B)),
+            _p(C), ctypes.c_int32(len(C)), ctypes.c_int32(w),
+            _p(rows_a), ctypes.c_int64(nrows),
+            _p(S), _p(N), _p(edge), _p(bi), _p(bs), _p(b2), _p(st),
+            ctypes.c_double(knot_eps), ctypes.c_int32(nthreads),
+            None if rst is None else ctypes.byref(rst))
     if rc != 0:
         raise ValueError("seis_oracle_crs: invalid arguments")
-    return Result(S=S, N=N, edge=edge, best_idx=bi, best_S=bs, second_S=b2, stack=st)
+    return Result(S=S, N=N, edge=edge, best_idx=bi, best_S=bs, second_S=b2, stack=st, **rng)
 
 
 def crs_eval(ds, nb, theta, w=11, rows=None, knot_eps=1e-4, nthreads=0) -> Result:
@@ -224,18 +252,24 @@ def crs_eval(ds, nb, theta, w=11, rows=None, knot_eps=1e-4, nthreads=0) -> Resul
     st = np.empty(nrows, np.float64)
     N = np.empty(nrows, np.int32)
     knot = np.empty(nrows, np.int8)
+    rng, rst = _ranges(nrows)
     rc = lib.seis_oracle_crs_eval(*[_p(a) for a in arrs], ctypes.c_int64(ncen), ctypes.c_int32(w),
                                   _p(rows_a), ctypes.c_int64(nrows), _p(theta),
                                   _p(S), _p(grad), _p(st), _p(N), _p(knot),
-                                  ctypes.c_double(knot_eps), ctypes.c_int32(nthreads))
+                                  ctypes.c_double(knot_eps), ctypes.c_int32(nthreads),
+                                  ctypes.byref(rst))
     if rc != 0:
         raise ValueError("seis_oracle_crs_eval: invalid arguments")
-    return Result(S=S, grad=grad, stack=st, N=N, knot=knot != 0)
+    rng.pop("stack_at")
+    return Result(S=S, grad=grad, stack=st, N=N, knot=knot != 0, **rng)
 
 
 def crs_refine(ds, nb, theta0, lo3, hi3, steps=20, step0=0.05, w=11, rows=None,
                nthreads=0) -> Result:
-    """Projected normalised-gradient ascent from theta0 (reading c16)."""
+    """Projected quasi-Newton (BFGS) gradient ascent from theta0 in normalised coordinates,
+    with step halving on rejected trials (reading c16).  Returns theta, S, grad, stack and
+    traj [nrows, steps, 5]: each trial's operator (A, B, C), its S and whether it was
+    accepted (NaN for trials never made)."""
     lib = _load()
     arrs = _crs_common(ds, nb)
     ncen = len(arrs[6])
@@ -247,14 +281,23 @@ def crs_refine(ds, nb, theta0, lo3, hi3, steps=20, step0=0.05, w=11, rows=None,
     S = np.empty(nrows, np.float64)
     grad = np.empty((nrows, 3), np.float64)
     st = np.empty(nrows, np.float64)
+    traj = np.empty((nrows, max(steps, 0), 5), np.float64)
     rc = lib.seis_oracle_crs_refine(*[_p(a) for a in arrs], ctypes.c_int64(ncen),
                                     ctypes.c_int32(w), _p(rows_a), ctypes.c_int64(nrows),
                                     _p(theta0), _p(lo3), _p(hi3), ctypes.c_int32(steps),
                                     ctypes.c_double(step0), _p(th), _p(S), _p(grad), _p(st),
-                                    ctypes.c_int32(nthreads))
+                                    ctypes.c_int32(nthreads), _p(traj))
     if rc != 0:
         raise ValueError("seis_oracle_crs_refine: invalid arguments")
-    return Result(theta=th, S=S, grad=grad, stack=st)
+    return Result(theta=th, S=S, grad=grad, stack=st, traj=traj)
+
+
+def bfgs_inverse_update(H, s, y):
+    """The refinement's BFGS update of a 3x3 inverse curvature estimate H with step s and
+    gradient change y (returns the updated copy)."""
+    H9 = _c(np.array(H, np.float64).reshape(9), np.float64).copy()
+    _load().seis_oracle_bfgs_inverse_update(_p(H9), _p(_c(s, np.float64)), _p(_c(y, np.float64)))
+    return H9.reshape(3, 3)
 
 
 def top_starts(S_cube, A, B, C, nstart):
@@ -281,6 +324,7 @@ def crs_refine_multi(ds, nb, starts, lo3, hi3, steps=20, step0=0.05, w=11, rows=
     for k in range(len(starts)):
         r = crs_refine(ds, nb, starts[k], lo3, hi3, steps=steps, step0=step0, w=w, rows=rows,
                        nthreads=nthreads)
+        r.pop("traj")
         if best is None:
             best = r
             continue

@@ -37,8 +37,8 @@
  *     central midpoint (the 2-D hyperbolic CRS operator in A, B, C);
  *   - gradient (not in the paper): chain rule through the traveltime and the linear
  *     interpolation with k and the participation mask held fixed;
- *   - refinement (not in the paper): projected normalised-gradient ascent, see
- *     seis_oracle_crs_refine.
+ *   - refinement (not in the paper): projected quasi-Newton (BFGS) gradient ascent in
+ *     normalised coordinates with step halving, see seis_oracle_crs_refine.
  *
  * All input arrays are the same FP32 arrays the CUDA path receives; every arithmetic
  * step here is carried out in FP64.
@@ -82,16 +82,12 @@ static int window_inside(double u, int64_t ns, int hw)
     return (kf - hw >= 0.0) && (kf + hw + 1.0 <= (double)(ns - 1));
 }
 
-/* One intersection, Algorithm 1 inner loop: interpolate v = (c[j+1]-c[j])*x + c[j]
- * along the window and accumulate the semblance numerator terms, the energy and the
- * linear stack.  Returns 1 if the trace took part. */
-static int intersect(const float* f, int64_t ns, double u, int hw,
-                     double* num, double* den, double* ac)
+/* Algorithm 1 inner loop for a trace intersected at window centre k with fraction x:
+ * interpolate v = (c[j+1]-c[j])*x + c[j] along the window and accumulate the semblance
+ * numerator terms, the energy and the linear stack. */
+static void accumulate_window(const float* f, int64_t k, double x, int hw,
+                              double* num, double* den, double* ac)
 {
-    if (!window_inside(u, ns, hw)) return 0;
-    double kf = floor(u);
-    int64_t k = (int64_t)kf;
-    double x = u - kf;
     for (int j = -hw; j <= hw; ++j) {
         double c0 = (double)f[k + j];
         double c1 = (double)f[k + j + 1];
@@ -100,6 +96,16 @@ static int intersect(const float* f, int64_t ns, double u, int hw,
         *den += v * v;
         *ac += v;
     }
+}
+
+/* One intersection at fractional sample u: k = floor(u), x = u - k.  Returns 1 if the
+ * trace took part. */
+static int intersect(const float* f, int64_t ns, double u, int hw,
+                     double* num, double* den, double* ac)
+{
+    if (!window_inside(u, ns, hw)) return 0;
+    double kf = floor(u);
+    accumulate_window(f, (int64_t)kf, u - kf, hw, num, den, ac);
     return 1;
 }
 
@@ -125,6 +131,175 @@ static int edge_sensitive(double u, int64_t ns, int hw, double eps)
 static int zero_moveout(double A, double B, double C, double dm, double h)
 {
     return A * dm == 0.0 && B * dm * dm == 0.0 && C * h * h == 0.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Admissible results of an FP32 evaluation (reading c5).  Where a participation test of a
+ * trace sits within eps of its threshold -- a mask edge within eps samples of u, or (CRS)
+ * t0 + A dm or t^2 within eps of zero -- FP32 rounding may decide it either way.  Such a
+ * trace is "flagged" and its admissible outcomes are listed: not taking part (where the
+ * test may exclude it), or taking part with window centre k at floor(u), or at either
+ * integer next to u when u lies within eps of one, with the fraction x = u - k clamped to
+ * [0, 1].  Every combination of the flagged traces' outcomes, added to the sums of the
+ * other traces, gives one admissible (S, stack, N); their minimum and maximum bound what a
+ * correct FP32 evaluation may return.  Entries with more than ORACLE_MAXFLAG flagged
+ * traces are left unresolved (NaN bounds). */
+#define ORACLE_MAXFLAG 6
+#define ORACLE_EDGE_EPS 1e-3   /* samples (and samples, samples^2 for p and t^2) */
+
+/* Optional per-entry outputs of the searches (per row for seis_oracle_crs_eval).  Any
+ * pointer may be NULL. */
+typedef struct {
+    double* S_lo;        /* admissible range of S                                   */
+    double* S_hi;
+    double* stack;       /* stack ac / (N w) (t0 window: s(t0) / M(t0)) at the entry */
+    double* st_lo;       /* admissible range of the stack                           */
+    double* st_hi;
+    int32_t* N_lo;       /* admissible range of N (t0 window: M(t0))                */
+    int32_t* N_hi;
+} oracle_ranges;
+
+typedef struct {
+    const float* f;      /* the trace's samples                                      */
+    int slot;            /* t0 window: the output-time offset j + hw of this sample  */
+    int n;               /* number of outcomes (1..3)                                */
+    int64_t k[3];        /* window centre, or -1: the trace does not take part       */
+    double x[3];
+} flagged_trace;
+
+static void add_outcome(flagged_trace* ft, int64_t k, double x)
+{
+    for (int i = 0; i < ft->n; ++i)
+        if (ft->k[i] == k) return;
+    ft->k[ft->n] = k;
+    ft->x[ft->n] = x;
+    ft->n++;
+}
+
+/* The admissible outcomes of a trace of ns samples intersected at u (NaN: no real
+ * traveltime); may_drop: a near-zero p or t^2 may also exclude it.  hw = 0 gives the
+ * one-sample window [k, k+1] of the t0-window semblance. */
+static void list_outcomes(flagged_trace* ft, const float* f, int64_t ns, double u, int hw,
+                          double eps, int may_drop, int slot)
+{
+    ft->f = f;
+    ft->slot = slot;
+    ft->n = 0;
+    if (may_drop || !(u == u)) add_outcome(ft, -1, 0.0);
+    if (!(u == u)) return;
+    double ks[2];
+    int nk = 0;
+    const double K0 = floor(u + 0.5);
+    if (fabs(u - K0) < eps) { ks[nk++] = K0 - 1.0; ks[nk++] = K0; }
+    else ks[nk++] = floor(u);
+    for (int i = 0; i < nk; ++i) {
+        const double kf = ks[i];
+        if (kf - hw >= 0.0 && kf + hw + 1.0 <= (double)(ns - 1)) {
+            double x = u - kf;
+            x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+            add_outcome(ft, (int64_t)kf, x);
+        } else {
+            add_outcome(ft, -1, 0.0);
+        }
+    }
+}
+
+static void widen(double v, double* lo, double* hi)
+{
+    if (v < *lo) *lo = v;
+    if (v > *hi) *hi = v;
+}
+
+/* Range over the outcome combinations of the flagged traces for the paper's window
+ * (Eq. 1, Algorithm 1); (num0, den0, ac0, N0) are the sums of the other traces.  The
+ * ranges start at the nominal values (S, st, N), so they always contain them. */
+static void ranges_window(const double* num0, double den0, double ac0, int64_t N0, int hw,
+                          const flagged_trace* ft, int nf, double S, double st, int64_t N,
+                          oracle_ranges* R, int64_t at)
+{
+    const int w = 2 * hw + 1;
+    double slo = S, shi = S, tlo = st, thi = st, nlo = (double)N, nhi = (double)N;
+    if (nf > ORACLE_MAXFLAG) {
+        slo = shi = tlo = thi = NAN;
+    } else if (nf > 0) {
+        int pick[ORACLE_MAXFLAG] = {0};
+        for (;;) {
+            double num[ORACLE_MAXW], den = den0, ac = ac0;
+            int64_t n = N0;
+            memcpy(num, num0, sizeof(double) * (size_t)w);
+            for (int q = 0; q < nf; ++q) {
+                const int a = pick[q];
+                if (ft[q].k[a] >= 0) {
+                    accumulate_window(ft[q].f, ft[q].k[a], ft[q].x[a], hw, num, &den, &ac);
+                    ++n;
+                }
+            }
+            widen(semblance_of(num, w, den, n), &slo, &shi);
+            widen(n ? ac / ((double)n * w) : 0.0, &tlo, &thi);
+            widen((double)n, &nlo, &nhi);
+            int q = 0;
+            while (q < nf && ++pick[q] == ft[q].n) { pick[q] = 0; ++q; }
+            if (q == nf) break;
+        }
+    }
+    if (R->S_lo) R->S_lo[at] = slo;
+    if (R->S_hi) R->S_hi[at] = shi;
+    if (R->stack) R->stack[at] = st;
+    if (R->st_lo) R->st_lo[at] = tlo;
+    if (R->st_hi) R->st_hi[at] = thi;
+    if (R->N_lo) R->N_lo[at] = (int32_t)nlo;
+    if (R->N_hi) R->N_hi[at] = (int32_t)nhi;
+}
+
+/* The same for the t0-window semblance (reading c18): per output-time offset j the sums
+ * s0[j], e0[j], M0[j] of the other traces; a flagged trace adds one interpolated sample
+ * to its own slot j. */
+static void ranges_t0win(const double* s0, const double* e0, const int64_t* M0, int w,
+                         const flagged_trace* ft, int nf, double S, double st, int64_t N,
+                         oracle_ranges* R, int64_t at)
+{
+    const int hw = w / 2;
+    double slo = S, shi = S, tlo = st, thi = st, nlo = (double)N, nhi = (double)N;
+    if (nf > ORACLE_MAXFLAG) {
+        slo = shi = tlo = thi = NAN;
+    } else if (nf > 0) {
+        int pick[ORACLE_MAXFLAG] = {0};
+        for (;;) {
+            double sj[ORACLE_MAXW], ej[ORACLE_MAXW];
+            int64_t Mj[ORACLE_MAXW];
+            memcpy(sj, s0, sizeof(double) * (size_t)w);
+            memcpy(ej, e0, sizeof(double) * (size_t)w);
+            memcpy(Mj, M0, sizeof(int64_t) * (size_t)w);
+            for (int q = 0; q < nf; ++q) {
+                const int a = pick[q];
+                const int64_t k = ft[q].k[a];
+                if (k < 0) continue;
+                const float* f = ft[q].f;
+                const double v = ((double)f[k + 1] - (double)f[k]) * ft[q].x[a] + (double)f[k];
+                sj[ft[q].slot] += v;
+                ej[ft[q].slot] += v * v;
+                Mj[ft[q].slot] += 1;
+            }
+            double num = 0.0, den = 0.0;
+            for (int j = 0; j < w; ++j) {
+                num += sj[j] * sj[j];
+                den += (double)Mj[j] * ej[j];
+            }
+            widen(den > 0.0 ? num / den : 0.0, &slo, &shi);
+            widen(Mj[hw] ? sj[hw] / (double)Mj[hw] : 0.0, &tlo, &thi);
+            widen((double)Mj[hw], &nlo, &nhi);
+            int q = 0;
+            while (q < nf && ++pick[q] == ft[q].n) { pick[q] = 0; ++q; }
+            if (q == nf) break;
+        }
+    }
+    if (R->S_lo) R->S_lo[at] = slo;
+    if (R->S_hi) R->S_hi[at] = shi;
+    if (R->stack) R->stack[at] = st;
+    if (R->st_lo) R->st_lo[at] = tlo;
+    if (R->st_hi) R->st_hi[at] = thi;
+    if (R->N_lo) R->N_lo[at] = (int32_t)nlo;
+    if (R->N_hi) R->N_hi[at] = (int32_t)nhi;
 }
 
 /* Output row r -> (owner index, local sample n) by binary search in off[0..cnt]. */
@@ -168,7 +343,7 @@ int seis_oracle_cmp(const float* traces, const int64_t* trace_off, const float* 
                     const int64_t* rows, int64_t nrows,
                     double* S, int32_t* Nvalid, int8_t* edge,
                     int32_t* best_idx, double* best_S, double* second_S, double* stack,
-                    double knot_eps, int32_t nthreads)
+                    double knot_eps, int32_t nthreads, oracle_ranges* R)
 {
     if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || nc < 1 || G < 1) return -1;
     const int hw = w / 2;
@@ -183,28 +358,41 @@ int seis_oracle_cmp(const float* traces, const int64_t* trace_off, const float* 
         const int64_t n = r - out_off[g];
         const double dtg = (double)dt[g];
         const double t0 = (double)n * dtg;
-        double num[ORACLE_MAXW];
+        double num[ORACLE_MAXW], num0[ORACLE_MAXW];
+        flagged_trace ft[ORACLE_MAXFLAG];
         int32_t bi = -1; double bs = -1.0, b2 = -1.0, bst = 0.0;
         for (int32_t c = 0; c < nc; ++c) {
             const double Cc = (double)C[c];
-            double den = 0.0, ac = 0.0; int64_t N = 0; int flag = 0;
+            double den = 0.0, ac = 0.0; int64_t N = 0; int nflag = 0;
+            double den0 = 0.0, ac0 = 0.0; int64_t N0 = 0;     /* unflagged traces (R) */
             memset(num, 0, sizeof(double) * (size_t)w);
+            memset(num0, 0, sizeof(double) * (size_t)w);
             for (int64_t i = gather_off[g]; i < gather_off[g + 1]; ++i) {
                 const double hi = (double)h[i];
                 const int64_t ns_i = trace_off[i + 1] - trace_off[i];
+                const float* f = traces + trace_off[i];
                 const double rad = t0 * t0 + Cc * hi * hi;            /* t^2, Section 2.1 */
                 if (!(rad >= 0.0)) continue;
                 const double u = sqrt(rad) / dtg;                      /* traveltime in samples */
-                if (edge && !zero_moveout(0.0, 0.0, Cc, 0.0, hi) &&
-                    edge_sensitive(u, ns_i, hw, knot_eps))
-                    flag = 1;
-                N += intersect(traces + trace_off[i], ns_i, u, hw, num, &den, &ac);
+                const int flagged = (edge || R) && !zero_moveout(0.0, 0.0, Cc, 0.0, hi) &&
+                                    edge_sensitive(u, ns_i, hw, knot_eps);
+                N += intersect(f, ns_i, u, hw, num, &den, &ac);
+                if (!R) { nflag += flagged; continue; }
+                if (flagged) {
+                    if (nflag < ORACLE_MAXFLAG)
+                        list_outcomes(&ft[nflag], f, ns_i, u, hw, knot_eps, 0, 0);
+                    ++nflag;
+                } else {
+                    N0 += intersect(f, ns_i, u, hw, num0, &den0, &ac0);
+                }
             }
             const double s = semblance_of(num, w, den, N);
+            const double st = N ? ac / ((double)N * w) : 0.0;
             if (S) S[e * nc + c] = s;
             if (Nvalid) Nvalid[e * nc + c] = (int32_t)N;
-            if (edge) edge[e * nc + c] = (int8_t)flag;
-            if (s > bs) { b2 = bs; bs = s; bi = c; bst = N ? ac / ((double)N * w) : 0.0; }
+            if (edge) edge[e * nc + c] = (int8_t)(nflag > 127 ? 127 : nflag);
+            if (R) ranges_window(num0, den0, ac0, N0, hw, ft, nflag, s, st, N, R, e * nc + c);
+            if (s > bs) { b2 = bs; bs = s; bi = c; bst = st; }
             else if (s > b2) b2 = s;
         }
         if (best_idx) best_idx[e] = bi;
@@ -239,7 +427,7 @@ int seis_oracle_cmp_t0win(const float* traces, const int64_t* trace_off, const f
                           const int64_t* rows, int64_t nrows,
                           double* S, int32_t* Nvalid, int8_t* edge,
                           int32_t* best_idx, double* best_S, double* second_S, double* stack,
-                          double knot_eps, int32_t nthreads)
+                          double knot_eps, int32_t nthreads, oracle_ranges* R)
 {
     if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || nc < 1 || G < 1) return -1;
     const int hw = w / 2;
@@ -253,11 +441,16 @@ int seis_oracle_cmp_t0win(const float* traces, const int64_t* trace_off, const f
         const int64_t n = r - out_off[g];
         const int64_t nrow_g = out_off[g + 1] - out_off[g];
         const double dtg = (double)dt[g];
+        double sb[ORACLE_MAXW], eb[ORACLE_MAXW];         /* unflagged traces per j (R) */
+        int64_t Mb[ORACLE_MAXW];
+        flagged_trace ft[ORACLE_MAXFLAG];
         int32_t bi = -1; double bs = -1.0, b2 = -1.0, bst = 0.0;
         for (int32_t c = 0; c < nc; ++c) {
             const double Cc = (double)C[c];
-            double num = 0.0, den = 0.0, s0 = 0.0; int64_t M0 = 0; int flag = 0;
+            double num = 0.0, den = 0.0, s0 = 0.0; int64_t M0 = 0; int nflag = 0;
             for (int j = -hw; j <= hw; ++j) {
+                sb[j + hw] = eb[j + hw] = 0.0;
+                Mb[j + hw] = 0;
                 const int64_t n2 = n + j;
                 if (n2 < 0 || n2 >= nrow_g) continue;
                 const double t0 = (double)n2 * dtg;
@@ -266,27 +459,34 @@ int seis_oracle_cmp_t0win(const float* traces, const int64_t* trace_off, const f
                     const double hi = (double)h[i];
                     const int64_t ns_i = trace_off[i + 1] - trace_off[i];
                     const double u = sqrt(t0 * t0 + Cc * hi * hi) / dtg;
-                    if (edge && !zero_moveout(0.0, 0.0, Cc, 0.0, hi) &&
-                        sample_inside(u - knot_eps, ns_i) != sample_inside(u + knot_eps, ns_i))
-                        flag = 1;
+                    const float* f = traces + trace_off[i];
+                    const int flagged = (edge || R) && !zero_moveout(0.0, 0.0, Cc, 0.0, hi) &&
+                        sample_inside(u - knot_eps, ns_i) != sample_inside(u + knot_eps, ns_i);
+                    if (flagged) {
+                        if (R && nflag < ORACLE_MAXFLAG)
+                            list_outcomes(&ft[nflag], f, ns_i, u, 0, knot_eps, 0, j + hw);
+                        ++nflag;
+                    }
                     if (!sample_inside(u, ns_i)) continue;
                     const int64_t k = (int64_t)floor(u);
                     const double x = u - (double)k;
-                    const float* f = traces + trace_off[i];
                     const double v = ((double)f[k + 1] - (double)f[k]) * x + (double)f[k];
                     sj += v;
                     ej += v * v;
                     ++Mj;
+                    if (!flagged) { sb[j + hw] += v; eb[j + hw] += v * v; Mb[j + hw] += 1; }
                 }
                 num += sj * sj;
                 den += (double)Mj * ej;
                 if (j == 0) { s0 = sj; M0 = Mj; }
             }
             const double sv = (den > 0.0) ? num / den : 0.0;
+            const double st = M0 ? s0 / (double)M0 : 0.0;
             if (S) S[e * nc + c] = sv;
             if (Nvalid) Nvalid[e * nc + c] = (int32_t)M0;
-            if (edge) edge[e * nc + c] = (int8_t)flag;
-            if (sv > bs) { b2 = bs; bs = sv; bi = c; bst = M0 ? s0 / (double)M0 : 0.0; }
+            if (edge) edge[e * nc + c] = (int8_t)(nflag > 127 ? 127 : nflag);
+            if (R) ranges_t0win(sb, eb, Mb, w, ft, nflag, sv, st, M0, R, e * nc + c);
+            if (sv > bs) { b2 = bs; bs = sv; bi = c; bst = st; }
             else if (sv > b2) b2 = sv;
         }
         if (best_idx) best_idx[e] = bi;
@@ -355,7 +555,7 @@ int seis_oracle_crs(const float* traces, const int64_t* trace_off, const float* 
                     const int64_t* rows, int64_t nrows,
                     double* S, int32_t* Nvalid, int8_t* edge,
                     int32_t* best_idx, double* best_S, double* second_S, double* stack,
-                    double knot_eps, int32_t nthreads)
+                    double knot_eps, int32_t nthreads, oracle_ranges* R)
 {
     if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || nA < 1 || nB < 1 || nC < 1 || n_central < 1)
         return -1;
@@ -373,39 +573,54 @@ int seis_oracle_crs(const float* traces, const int64_t* trace_off, const float* 
         const double dtg = (double)dt_c[c];
         const double t0 = (double)n * dtg;
         const double mc = (double)m_c[c];
-        double num[ORACLE_MAXW];
+        double num[ORACLE_MAXW], num0[ORACLE_MAXW];
+        flagged_trace ft[ORACLE_MAXFLAG];
         int32_t bi = -1; double bs = -1.0, b2 = -1.0, bst = 0.0;
         for (int64_t cand = 0; cand < ncand; ++cand) {
             const int64_t ia = cand / ((int64_t)nB * nC);
             const int64_t ib = (cand / nC) % nB;
             const int64_t ic = cand % nC;
             const double Av = (double)A[ia], Bv = (double)B[ib], Cv = (double)C[ic];
-            double den = 0.0, ac = 0.0; int64_t N = 0; int flag = 0;
+            double den = 0.0, ac = 0.0; int64_t N = 0; int nflag = 0;
+            double den0 = 0.0, ac0 = 0.0; int64_t N0 = 0;     /* unflagged traces (R) */
             memset(num, 0, sizeof(double) * (size_t)w);
+            memset(num0, 0, sizeof(double) * (size_t)w);
             for (int64_t q = nbr_off[c]; q < nbr_off[c + 1]; ++q) {
                 const int64_t i = nbr_trace[q];
                 const double dm = (double)m[i] - mc;
                 const int64_t ns_i = trace_off[i + 1] - trace_off[i];
+                const float* f = traces + trace_off[i];
                 double u, p;
                 const double rad = (t0 + Av * dm) * (t0 + Av * dm) + Bv * dm * dm
                                    + Cv * (double)h[i] * (double)h[i];
                 const int exact = zero_moveout(Av, Bv, Cv, dm, (double)h[i]);
-                if (edge) {
-                    /* participation flips for a tiny change of p = t0 + A dm or of t^2
-                     * (p is exact when A dm = 0, t^2 when every moveout term is 0) */
-                    if ((Av * dm != 0.0 && fabs(t0 + Av * dm) < knot_eps * dtg) ||
-                        (!exact && fabs(rad) < knot_eps * dtg * dtg))
-                        flag = 1;
+                /* participation flips for a tiny change of p = t0 + A dm or of t^2
+                 * (p is exact when A dm = 0, t^2 when every moveout term is 0) */
+                const int drop = (edge || R) &&
+                                 ((Av * dm != 0.0 && fabs(t0 + Av * dm) < knot_eps * dtg) ||
+                                  (!exact && fabs(rad) < knot_eps * dtg * dtg));
+                const int real = crs_time(t0, Av, Bv, Cv, dm, (double)h[i], dtg, &u, &p, NULL);
+                const int flagged = drop || ((edge || R) && real && !exact &&
+                                             edge_sensitive(u, ns_i, hw, knot_eps));
+                if (real) N += intersect(f, ns_i, u, hw, num, &den, &ac);
+                if (!R) { nflag += flagged; continue; }
+                if (flagged) {
+                    const double ua = real ? u : sqrt(rad > 0.0 ? rad : 0.0) / dtg;
+                    if (nflag < ORACLE_MAXFLAG)
+                        list_outcomes(&ft[nflag], f, ns_i, ua, hw, knot_eps, drop, 0);
+                    ++nflag;
+                } else if (real) {
+                    N0 += intersect(f, ns_i, u, hw, num0, &den0, &ac0);
                 }
-                if (!crs_time(t0, Av, Bv, Cv, dm, (double)h[i], dtg, &u, &p, NULL)) continue;
-                if (edge && !exact && edge_sensitive(u, ns_i, hw, knot_eps)) flag = 1;
-                N += intersect(traces + trace_off[i], ns_i, u, hw, num, &den, &ac);
             }
             const double s = semblance_of(num, w, den, N);
+            const double st = N ? ac / ((double)N * w) : 0.0;
             if (S) S[e * ncand + cand] = s;
             if (Nvalid) Nvalid[e * ncand + cand] = (int32_t)N;
-            if (edge) edge[e * ncand + cand] = (int8_t)flag;
-            if (s > bs) { b2 = bs; bs = s; bi = (int32_t)cand; bst = N ? ac / ((double)N * w) : 0.0; }
+            if (edge) edge[e * ncand + cand] = (int8_t)(nflag > 127 ? 127 : nflag);
+            if (R) ranges_window(num0, den0, ac0, N0, hw, ft, nflag, s, st, N, R,
+                                 e * ncand + cand);
+            if (s > bs) { b2 = bs; bs = s; bi = (int32_t)cand; bst = st; }
             else if (s > b2) b2 = s;
         }
         if (best_idx) best_idx[e] = bi;
@@ -431,7 +646,7 @@ int seis_oracle_crs_t0win(const float* traces, const int64_t* trace_off, const f
                           const int64_t* rows, int64_t nrows,
                           double* S, int32_t* Nvalid, int8_t* edge,
                           int32_t* best_idx, double* best_S, double* second_S, double* stack,
-                          double knot_eps, int32_t nthreads)
+                          double knot_eps, int32_t nthreads, oracle_ranges* R)
 {
     if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || nA < 1 || nB < 1 || nC < 1 || n_central < 1)
         return -1;
@@ -448,13 +663,18 @@ int seis_oracle_crs_t0win(const float* traces, const int64_t* trace_off, const f
         const int64_t nrow_c = out_off_c[c + 1] - out_off_c[c];
         const double dtg = (double)dt_c[c];
         const double mc = (double)m_c[c];
+        double sb[ORACLE_MAXW], eb[ORACLE_MAXW];         /* unflagged traces per j (R) */
+        int64_t Mb[ORACLE_MAXW];
+        flagged_trace ft[ORACLE_MAXFLAG];
         int32_t bi = -1; double bs = -1.0, b2 = -1.0, bst = 0.0;
         for (int64_t cand = 0; cand < ncand; ++cand) {
             const double Av = (double)A[cand / ((int64_t)nB * nC)];
             const double Bv = (double)B[(cand / nC) % nB];
             const double Cv = (double)C[cand % nC];
-            double num = 0.0, den = 0.0, s0 = 0.0; int64_t M0 = 0; int flag = 0;
+            double num = 0.0, den = 0.0, s0 = 0.0; int64_t M0 = 0; int nflag = 0;
             for (int j = -hw; j <= hw; ++j) {
+                sb[j + hw] = eb[j + hw] = 0.0;
+                Mb[j + hw] = 0;
                 const int64_t n2 = n + j;
                 if (n2 < 0 || n2 >= nrow_c) continue;
                 const double t0 = (double)n2 * dtg;
@@ -464,34 +684,42 @@ int seis_oracle_crs_t0win(const float* traces, const int64_t* trace_off, const f
                     const double dm = (double)m[i] - mc;
                     const double hi = (double)h[i];
                     const int64_t ns_i = trace_off[i + 1] - trace_off[i];
+                    const float* f = traces + trace_off[i];
                     const double rad = (t0 + Av * dm) * (t0 + Av * dm) + Bv * dm * dm + Cv * hi * hi;
                     const int exact = zero_moveout(Av, Bv, Cv, dm, hi);
-                    if (edge && ((Av * dm != 0.0 && fabs(t0 + Av * dm) < knot_eps * dtg) ||
-                                 (!exact && fabs(rad) < knot_eps * dtg * dtg)))
-                        flag = 1;
+                    const int drop = (edge || R) &&
+                                     ((Av * dm != 0.0 && fabs(t0 + Av * dm) < knot_eps * dtg) ||
+                                      (!exact && fabs(rad) < knot_eps * dtg * dtg));
                     double u, p;
-                    if (!crs_time(t0, Av, Bv, Cv, dm, hi, dtg, &u, &p, NULL)) continue;
-                    if (edge && !exact &&
-                        sample_inside(u - knot_eps, ns_i) != sample_inside(u + knot_eps, ns_i))
-                        flag = 1;
-                    if (!sample_inside(u, ns_i)) continue;
+                    const int real = crs_time(t0, Av, Bv, Cv, dm, hi, dtg, &u, &p, NULL);
+                    const int flagged = drop || ((edge || R) && real && !exact &&
+                        sample_inside(u - knot_eps, ns_i) != sample_inside(u + knot_eps, ns_i));
+                    if (flagged) {
+                        const double ua = real ? u : sqrt(rad > 0.0 ? rad : 0.0) / dtg;
+                        if (R && nflag < ORACLE_MAXFLAG)
+                            list_outcomes(&ft[nflag], f, ns_i, ua, 0, knot_eps, drop, j + hw);
+                        ++nflag;
+                    }
+                    if (!real || !sample_inside(u, ns_i)) continue;
                     const int64_t k = (int64_t)floor(u);
                     const double x = u - (double)k;
-                    const float* f = traces + trace_off[i];
                     const double v = ((double)f[k + 1] - (double)f[k]) * x + (double)f[k];
                     sj += v;
                     ej += v * v;
                     ++Mj;
+                    if (!flagged) { sb[j + hw] += v; eb[j + hw] += v * v; Mb[j + hw] += 1; }
                 }
                 num += sj * sj;
                 den += (double)Mj * ej;
                 if (j == 0) { s0 = sj; M0 = Mj; }
             }
             const double sv = (den > 0.0) ? num / den : 0.0;
+            const double st = M0 ? s0 / (double)M0 : 0.0;
             if (S) S[e * ncand + cand] = sv;
             if (Nvalid) Nvalid[e * ncand + cand] = (int32_t)M0;
-            if (edge) edge[e * ncand + cand] = (int8_t)flag;
-            if (sv > bs) { b2 = bs; bs = sv; bi = (int32_t)cand; bst = M0 ? s0 / (double)M0 : 0.0; }
+            if (edge) edge[e * ncand + cand] = (int8_t)(nflag > 127 ? 127 : nflag);
+            if (R) ranges_t0win(sb, eb, Mb, w, ft, nflag, sv, st, M0, R, e * ncand + cand);
+            if (sv > bs) { b2 = bs; bs = sv; bi = (int32_t)cand; bst = st; }
             else if (sv > b2) b2 = sv;
         }
         if (best_idx) best_idx[e] = bi;
@@ -515,22 +743,44 @@ static void crs_eval_one(const float* traces, const int64_t* trace_off, const fl
                          const float* m, const int32_t* list, int64_t cnt, double mc,
                          double t0, double dtg, int hw, const double* th,
                          double* S_out, double* grad_out, double* stack_out, int32_t* N_out,
-                         int8_t* knot_out, double knot_eps)
+                         int8_t* knot_out, double knot_eps, oracle_ranges* R, int64_t at)
 {
     int knot = 0;
     const int w = 2 * hw + 1;
-    double num[ORACLE_MAXW], dnum[3][ORACLE_MAXW];
+    double num[ORACLE_MAXW], dnum[3][ORACLE_MAXW], num0[ORACLE_MAXW];
     double den = 0.0, ac = 0.0, dden[3] = {0.0, 0.0, 0.0};
-    int64_t N = 0;
+    double den0 = 0.0, ac0 = 0.0;                 /* unflagged traces (R, reading c5) */
+    int64_t N = 0, N0 = 0;
+    int nflag = 0;
+    flagged_trace ft[ORACLE_MAXFLAG];
     memset(num, 0, sizeof(num));
     memset(dnum, 0, sizeof(dnum));
+    memset(num0, 0, sizeof(num0));
     for (int64_t q = 0; q < cnt; ++q) {
         const int64_t i = list[q];
         const double dm = (double)m[i] - mc;
         const double hh = (double)h[i];
         const int64_t ns_i = trace_off[i + 1] - trace_off[i];
-        double u, p, t;
-        if (!crs_time(t0, th[0], th[1], th[2], dm, hh, dtg, &u, &p, &t)) continue;
+        double u = 0.0, p = 0.0, t = 0.0;
+        const int real = crs_time(t0, th[0], th[1], th[2], dm, hh, dtg, &u, &p, &t);
+        if (R) {
+            const double eps = ORACLE_EDGE_EPS;
+            const double pp = t0 + th[0] * dm;
+            const double rad = pp * pp + th[1] * dm * dm + th[2] * hh * hh;
+            const int exact = zero_moveout(th[0], th[1], th[2], dm, hh);
+            const int drop = (th[0] * dm != 0.0 && fabs(pp) < eps * dtg) ||
+                             (!exact && fabs(rad) < eps * dtg * dtg);
+            const int flagged = drop || (real && !exact && edge_sensitive(u, ns_i, hw, eps));
+            if (flagged) {
+                const double ua = real ? u : sqrt(rad > 0.0 ? rad : 0.0) / dtg;
+                if (nflag < ORACLE_MAXFLAG)
+                    list_outcomes(&ft[nflag], traces + trace_off[i], ns_i, ua, hw, eps, drop, 0);
+                ++nflag;
+            } else if (real) {
+                N0 += intersect(traces + trace_off[i], ns_i, u, hw, num0, &den0, &ac0);
+            }
+        }
+        if (!real) continue;
         /* knot bookkeeping for FP32 parity of the gradient (defined almost everywhere):
          * u within the FP32 error of u of a sample, or a mask edge within it */
         if (knot_out && !zero_moveout(th[0], th[1], th[2], dm, hh)) {
@@ -580,6 +830,11 @@ static void crs_eval_one(const float* traces, const int64_t* trace_off, const fl
     if (stack_out) *stack_out = N ? ac / ((double)N * w) : 0.0;
     if (N_out) *N_out = (int32_t)N;
     if (knot_out) *knot_out = (int8_t)knot;
+    if (R) {
+        const double S = (N == 0 || !(den > 0.0)) ? 0.0 : nu / ((double)N * den);
+        ranges_window(num0, den0, ac0, N0, hw, ft, nflag, S, N ? ac / ((double)N * w) : 0.0, N,
+                      R, at);
+    }
 }
 
 /* Evaluate S, dS/d(A,B,C) and the stack at given operators, one per row. */
@@ -589,7 +844,7 @@ int seis_oracle_crs_eval(const float* traces, const int64_t* trace_off, const fl
                          int64_t n_central, int32_t w,
                          const int64_t* rows, int64_t nrows, const double* theta,
                          double* S, double* grad, double* stack, int32_t* Nvalid,
-                         int8_t* knot, double knot_eps, int32_t nthreads)
+                         int8_t* knot, double knot_eps, int32_t nthreads, oracle_ranges* R)
 {
     if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || n_central < 1) return -1;
     const int hw = w / 2;
@@ -604,7 +859,8 @@ int seis_oracle_crs_eval(const float* traces, const int64_t* trace_off, const fl
         double s, st; int32_t N;
         crs_eval_one(traces, trace_off, h, m, nbr_trace + nbr_off[c], nbr_off[c + 1] - nbr_off[c],
                      (double)m_c[c], (double)n * dtg, dtg, hw, theta + 3 * e,
-                     &s, grad ? grad + 3 * e : NULL, &st, &N, knot ? knot + e : NULL, knot_eps);
+                     &s, grad ? grad + 3 * e : NULL, &st, &N, knot ? knot + e : NULL, knot_eps,
+                     R, e);
         if (S) S[e] = s;
         if (stack) stack[e] = st;
         if (Nvalid) Nvalid[e] = N;
@@ -647,6 +903,18 @@ static void bfgs_inverse_update(double H[3][3], const double* s, const double* y
         for (int j = 0; j < 3; ++j) H[i][j] = N[i][j];
 }
 
+/* The BFGS update of a 3x3 inverse curvature estimate H (row-major, in place) with step s
+ * and gradient change y, as the refinement applies it (exported for the pins). */
+void seis_oracle_bfgs_inverse_update(double* H9, const double* s, const double* y)
+{
+    double H[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) H[i][j] = H9[3 * i + j];
+    bfgs_inverse_update(H, s, y, dot3(s, y));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) H9[3 * i + j] = H[i][j];
+}
+
 /* Gradient-ascent refinement of the CRS operator from a coarse pick (reading c16).
  * Per row, in normalised coordinates z = (theta - lo) / (hi - lo), g = dS/dz, a projected
  * quasi-Newton (BFGS) ascent with step halving:
@@ -661,7 +929,9 @@ static void bfgs_inverse_update(double H[3][3], const double* s, const double* y
  *       accept (z, S, g) <- (z', S', g'); a = 1;
  *     else a <- a/2.
  * Outputs theta_out [nrows*3], S_out, grad_out (dS/dtheta at the final point, may be
- * NULL), stack_out (may be NULL). */
+ * NULL), stack_out (may be NULL), and traj (may be NULL): for every row e and trial it,
+ * traj[(e*steps + it)*5 + 0..4] = the trial operator (A, B, C), its S, and 1 if it was
+ * accepted (0 if not); trials never made (the gradient vanished) are NaN. */
 int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const float* h,
                            const float* m, const int64_t* nbr_off, const int32_t* nbr_trace,
                            const float* m_c, const int64_t* out_off_c, const float* dt_c,
@@ -669,7 +939,7 @@ int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const 
                            const int64_t* rows, int64_t nrows, const double* theta_in,
                            const double* lo3, const double* hi3, int32_t steps, double step0,
                            double* theta_out, double* S_out, double* grad_out, double* stack_out,
-                           int32_t nthreads)
+                           int32_t nthreads, double* traj)
 {
     if (w < 1 || (w % 2) == 0 || w > ORACLE_MAXW || n_central < 1 || steps < 0) return -1;
     for (int a = 0; a < 3; ++a) if (!(hi3[a] > lo3[a])) return -1;
@@ -691,11 +961,13 @@ int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const 
             th[a] = theta_in[3 * e + a];
         }
         crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th, &s, g, &st, NULL,
-                     NULL, 0.0);
+                     NULL, 0.0, NULL, 0);
         double span[3], H[3][3], al = 1.0;
         for (int a = 0; a < 3; ++a) span[a] = hi3[a] - lo3[a];
         for (int a = 0; a < 3; ++a) gz[a] = g[a] * span[a];
         reset_inverse_curvature(H, gz, step0);
+        if (traj)
+            for (int q = 0; q < 5 * steps; ++q) traj[e * 5 * steps + q] = NAN;
         for (int it = 0; it < steps; ++it) {
             for (int a = 0; a < 3; ++a) gz[a] = g[a] * span[a];
             if (!(norm3(gz) > 0.0)) break;
@@ -714,7 +986,12 @@ int seis_oracle_crs_refine(const float* traces, const int64_t* trace_off, const 
                 th2[a] = lo3[a] + z2[a] * span[a];
             }
             crs_eval_one(traces, trace_off, h, m, list, cnt, mc, t0, dtg, hw, th2, &s2, g2, &st2,
-                         NULL, NULL, 0.0);
+                         NULL, NULL, 0.0, NULL, 0);
+            if (traj) {
+                double* tr = traj + (e * steps + it) * 5;
+                tr[0] = th2[0]; tr[1] = th2[1]; tr[2] = th2[2]; tr[3] = s2;
+                tr[4] = s2 >= s ? 1.0 : 0.0;
+            }
             if (s2 >= s) {
                 double sv[3], yv[3];
                 for (int a = 0; a < 3; ++a) {

@@ -61,7 +61,7 @@ def test_batch_matches_oracle_per_item(seis, small):
         kinds.add(int(it["kind"]))
         sl = slice(r0, r0 + rows)
         parity.check_picks(got["best_idx"][sl], got["best_S"][sl], got["stack"][sl], ref,
-                           f"batch item {r0}", edge=ref.edge)
+                           f"batch item {r0}")
     assert kinds == {0, 1}
 
 
@@ -160,6 +160,5 @@ def test_batch_workload_distributions_sampled(seis):
             ref = oracle.crs_semblance(sub, nb, Ai, Bi, Ci, w=11, rows=sel, want_cube=True)
         kinds.add(int(it["kind"]))
         parity.check_picks(got["best_idx"][r0 + sel], got["best_S"][r0 + sel],
-                           got["stack"][r0 + sel], ref, f"batch workload item {idx}",
-                           edge=ref.edge)
+                           got["stack"][r0 + sel], ref, f"batch workload item {idx}")
     assert kinds == {0, 1}

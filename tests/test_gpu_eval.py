@@ -54,12 +54,8 @@ def test_stack_cmp_matches_oracle(seis):
     seis.device_status()
     th = np.stack([np.zeros(rows), np.zeros(rows), C.astype(np.float64)], 1)
     ref = oracle.crs_eval(ds, oracle.cmp_as_crs(ds), th)
-    np.testing.assert_array_equal(out["N"].cpu().numpy(), ref.N)
-    dS = np.abs(out["S"].cpu().numpy() - ref.S).max()
-    st = out["stack"].cpu().numpy()
-    rel = np.linalg.norm(st - ref.stack) / np.linalg.norm(ref.stack)
-    print(f"[parity] stack-cmp: max dS {dS:.2e} stack rel L2 {rel:.2e}")
-    assert dS <= parity.S_TOL and rel <= parity.STACK_TOL
+    parity.check_eval(out["S"].cpu().numpy(), out["stack"].cpu().numpy(),
+                      out["N"].cpu().numpy(), ref, "stack-cmp")
 
 
 def test_stack_matches_search_pick(seis):
@@ -81,14 +77,11 @@ def test_stack_crs_matches_oracle(seis, line):
     torch.cuda.synchronize()
     seis.device_status()
     ref = oracle.crs_eval(ds, ap.oracle_nb, th.astype(np.float64))
-    N = out["N"].cpu().numpy()
-    agree = N == ref.N
-    assert agree.mean() > 0.995
-    dS = np.abs(out["S"].cpu().numpy() - ref.S)[agree].max()
-    st = out["stack"].cpu().numpy()
-    rel = np.linalg.norm((st - ref.stack)[agree]) / np.linalg.norm(ref.stack[agree])
-    print(f"[parity] stack-crs: max dS {dS:.2e} stack rel L2 {rel:.2e} N agree {agree.mean():.4f}")
-    assert dS <= parity.S_TOL and rel <= parity.STACK_TOL
+    # every row: N, S and the stack inside the oracle's admissible ranges (a row where FP32
+    # may decide a trace's participation either way has the range of both outcomes)
+    rep = parity.check_eval(out["S"].cpu().numpy(), out["stack"].cpu().numpy(),
+                            out["N"].cpu().numpy(), ref, "stack-crs")
+    assert rep["flagged"] < 0.05
 
 
 def test_adjoint_matches_oracle_gradient(seis, line):
@@ -157,6 +150,99 @@ def test_refine_monotone_and_consistent(seis, line, coarse_starts):
     print(f"[parity] refine: gain {np.mean(S1 - S0):.4f}, |S_gpu - S_oracle| <= 1e-3 on "
           f"{close.mean():.3f} of rows, mean diff {np.mean(S1 - ref.S):+.2e}")
     assert close.mean() >= 0.9
+
+
+@pytest.mark.parametrize("steps", [1, 2])
+def test_refine_steps_elementwise(seis, line, coarse_starts, steps):
+    """One and two refinement trials from the oracle's best coarse candidates, compared with
+    the oracle's trajectory element by element.  The trial direction is d = H g, so an FP32
+    gradient with relative error e moves the trial by about 2 e |d|; the GPU's gradient
+    error is measured at the start and at the oracle's trial points (the adjoint entry point
+    runs the refinement's evaluation kernel), and each row's operator must land within the
+    first-order bound that these errors give (BFGS step: the errors of g1 and of
+    y = g0 - g1 relative to |y|).  Rows are compared where the start and every trial are
+    knot-free (the gradient is defined in both precisions) and every accept decision is
+    clear (|S' - S| > 5e-5)."""
+    ds, g, ap = line
+    lo, hi = _ranges()
+    span = hi - lo
+    nb = ap.oracle_nb
+    _, starts = coarse_starts
+    th0 = starts[0].astype(np.float32)
+    r = seis.crs_refine(g, ap, torch.from_numpy(th0).cuda(), lo, hi, steps=steps, step0=0.05,
+                        w=11)
+    torch.cuda.synchronize()
+    seis.device_status()
+    ref = oracle.crs_refine(ds, nb, th0.astype(np.float64), lo, hi, steps=steps, step0=0.05)
+
+    def gpu_grad(th):
+        _, G, _ = seis.crs_semblance_grad(g, ap, torch.from_numpy(th.astype(np.float32)).cuda(),
+                                          w=11)
+        return G.cpu().numpy().astype(np.float64) * span
+
+    pts = [th0.astype(np.float64)] + [np.nan_to_num(ref.traj[:, it, :3]) for it in range(steps)]
+    ev = [oracle.crs_eval(ds, nb, p) for p in pts]
+    gz = [e.grad * span for e in ev]                               # dS/dz, oracle
+    err = [np.linalg.norm(gpu_grad(p) - q, axis=1) for p, q in zip(pts, gz)]
+    nrm = [np.linalg.norm(q, axis=1) for q in gz]
+    robust = (ev[0].S > 0.02) & ~ev[0].knot & (nrm[0] > 0)
+    S_prev = ev[0].S.copy()
+    for it in range(steps):
+        tr = ref.traj[:, it]
+        robust &= ~np.isnan(tr[:, 3]) & ~ev[it + 1].knot & (np.abs(tr[:, 3] - S_prev) > 5e-5)
+        S_prev = np.where(tr[:, 4] == 1.0, tr[:, 3], S_prev)
+    z = lambda th: (th - lo) / span
+    rel0 = err[0] / np.maximum(nrm[0], 1e-30)
+    tol1 = 1e-6 + 2.0 * 0.05 * rel0                                # |d1| = step0 = 0.05
+    acc1 = ref.traj[:, 0, 4] == 1.0
+    if steps == 1:
+        tol = np.where(acc1, tol1, 1e-6)
+    else:
+        acc2 = ref.traj[:, 1, 4] == 1.0
+        sv = z(ref.traj[:, 0, :3]) - z(pts[0])
+        yv = gz[0] - gz[1]
+        s_n, y_n = np.linalg.norm(sv, axis=1), np.linalg.norm(yv, axis=1)
+        kappa = s_n * y_n / np.maximum(np.abs(np.sum(sv * yv, axis=1)), 1e-300)
+        ey = (err[0] + err[1]) / np.maximum(y_n, 1e-30)
+        rel1 = err[1] / np.maximum(nrm[1], 1e-30)
+        # d2 = H1 g1 with H1 = V'H0V + rho s s', V = I - rho y s', H0 = (0.05/|g0|) I: the
+        # sizes of its two terms, times the relative errors of g0 (H0's scale), g1, and y
+        # (which enters through rho = 1/(s.y), amplified by kappa = |s||y|/|s.y|)
+        T = nrm[1] * (0.05 / np.maximum(nrm[0], 1e-30) * (1.0 + kappa) ** 2
+                      + kappa * s_n / np.maximum(y_n, 1e-30))
+        tol2_acc = tol1 * (1.0 + 2.0 * kappa) + T * (rel0 + rel1 + 2.0 * kappa * ey)
+        tol2_rej = 1e-6 + 0.5 * (tol1 - 1e-6)                              # halved first trial
+        tol_trial2 = np.where(acc1, tol2_acc, tol2_rej)
+        tol = np.where(acc2, tol_trial2, np.where(acc1, tol1, 1e-6))
+    th_g = r["theta"].cpu().numpy().astype(np.float64)
+    dz = np.linalg.norm(z(th_g) - z(ref.theta), axis=1)
+    # the GPU's final operator is knot-free too, so its S and gradient are continuous there
+    eg = oracle.crs_eval(ds, nb, th_g)
+    robust &= ~eg.knot
+    sel = robust
+    S_g = r["S"].cpu().numpy().astype(np.float64)
+    G_g = r["grad"].cpu().numpy().astype(np.float64) * span
+    dS = np.abs(S_g - ref.S)
+    dG = np.linalg.norm(G_g - eg.grad * span, axis=1)
+    nG = np.linalg.norm(eg.grad * span, axis=1)
+    print(f"[parity] refine {steps} step(s): {sel.sum()} of {len(sel)} rows compared; "
+          f"|dz| max {dz[sel].max():.2e}, 99th pct {np.percentile(dz[sel], 99):.2e}, "
+          f"max |dz|/bound {np.max(dz[sel] / tol[sel]):.2f}; max |dS| {dS[sel].max():.2e}; "
+          f"grad at the GPU's operator: median rel {np.median(dG[sel] / nG[sel]):.2e}")
+    assert sel.mean() > 0.3
+    bad = sel & (dz > tol)
+    assert not bad.any(), (f"{bad.sum()} rows beyond the FP32 bound, e.g. row "
+                           f"{np.nonzero(bad)[0][0]}: |dz| {dz[bad][0]:.2e} > {tol[bad][0]:.2e}")
+    # S: the oracle's S at its own point, plus the first-order change over |dz|
+    assert np.all(dS[sel] <= parity.S_TOL + nrm[-1][sel] * dz[sel] * 2.0 + 1e-6)
+    # the reported S and gradient are the evaluation at the reported operator: against the
+    # oracle there (relative 1e-3 of the gradient, with an FP32 floor)
+    assert np.all(np.abs(S_g - eg.S)[sel] <= parity.S_TOL)
+    # the gradient is the evaluation kernel's at the reported operator, bit for bit, and that
+    # kernel's gradient matches the oracle's there as the adjoint test requires
+    np.testing.assert_array_equal(G_g, gpu_grad(th_g.astype(np.float32)))
+    rel = np.linalg.norm((G_g - eg.grad * span)[sel]) / np.linalg.norm((eg.grad * span)[sel])
+    assert rel <= 1e-3 and np.median(dG[sel] / nG[sel]) <= 1e-3, rel
 
 
 def test_top_starts_exact(seis):

@@ -82,7 +82,7 @@ def test_every_cmp_variant_bit_identical_and_matches_oracle(seis, case):
     ref = oracle.cmp_semblance(ds, C)
     parity.check_cube(outs[0]["S"], ref, f"variants cmp {case}")
     parity.check_picks(outs[0]["best_idx"], outs[0]["best_S"], outs[0]["stack"], ref,
-                       f"variants cmp {case}", edge=ref.edge)
+                       f"variants cmp {case}")
 
 
 def test_every_crs_variant_bit_identical_and_matches_oracle(seis):
@@ -102,7 +102,7 @@ def test_every_crs_variant_bit_identical_and_matches_oracle(seis):
     ref = oracle.crs_semblance(ds, oracle.aperture(ds, central, 30.0), A, B, C, want_cube=True)
     parity.check_cube(outs[0]["S"], ref, "variants crs")
     parity.check_picks(outs[0]["best_idx"], outs[0]["best_S"], outs[0]["stack"], ref,
-                       "variants crs", edge=ref.edge)
+                       "variants crs")
 
 
 @pytest.mark.slow
@@ -126,8 +126,7 @@ def test_cmp_line_full_size_in_the_benchmark_configuration(seis):
     rows = np.sort(np.random.default_rng(3).choice(int(ds["out_off"][-1]), 512, replace=False))
     ref = oracle.cmp_semblance(ds, C, rows=rows)
     rep = parity.check_picks(got["best_idx"][rows], got["best_S"][rows], got["stack"][rows],
-                             ref, "cmp-line (bench variant)",
-                             edge=ref.edge)
+                             ref, "cmp-line (bench variant)")
     assert rep["pick_agree"] > 0.98
 
 
@@ -153,12 +152,11 @@ def test_crs_line_slice_in_the_benchmark_configuration(seis):
         seis.device_status()
     finally:
         seis.autotune_clear()
-    # most rows of this noisy line have near-ties (top-two gap < 1e-4, waived), so sample
-    # enough of them to compare a few dozen picks
+    # most rows of this noisy line have near-ties (top-two gap < 1e-4), where any admissible
+    # argmax is correct, so sample enough rows to hold a few dozen clear picks as well
     rows = np.sort(np.random.default_rng(4).choice(ap.rows, 96, replace=False))
     ref = oracle.crs_semblance(ds, oracle.aperture(ds, central, ds["apm"]), A, B, C,
                                rows=rows, want_cube=True)
     rep = parity.check_picks(got["best_idx"][rows], got["best_S"][rows], got["stack"][rows],
-                             ref, "crs-line (bench variant)",
-                             edge=ref.edge)
-    assert rep["pick_agree"] >= 0.9 and rep["waived"] < 0.9
+                             ref, "crs-line (bench variant)")
+    assert rep["pick_agree"] >= 0.9 and rep["clear_rows"] > 0.1

@@ -564,3 +564,105 @@ def test_invalid_arguments():
         oracle.cmp_semblance(ds, [1e-6], w=4)
     with pytest.raises(ValueError):
         oracle.cmp_semblance(ds, [1e-6], w=0)
+
+
+# --- admissible ranges where FP32 may decide a trace's participation either way (c5) ---
+
+def _window_S(windows, w):
+    """Eq. 1 (with 1/N) and Algorithm 1's stack from the traces' interpolated windows."""
+    if not windows:
+        return 0.0, 0.0
+    num = [sum(v[j] for v in windows) for j in range(w)]
+    den = sum(x * x for v in windows for x in v)
+    N = len(windows)
+    S = sum(a * a for a in num) / (N * den) if den > 0 else 0.0
+    return S, sum(sum(v) for v in windows) / (N * w)
+
+
+def test_admissible_range_at_mask_edges_bruteforce():
+    """Row 3 (dt = 1/256 s, C = 2^-20): trace 0 (h = 16 m, 8 samples) meets u = 5 exactly,
+    where w = 5 needs k + 3 <= 7, so it is out in exact arithmetic but in at k = 4, x = 1 for
+    an FP32 u a hair below 5.  Row 0: trace 1 (h = 8 m) meets u = 2 = hw exactly, in at
+    k = 2, x = 0, but out for u a hair below 2.  The oracle's range of S, stack and N must be
+    the min / max over exactly those two outcomes (computed here by brute force with
+    numpy.interp); entries with no trace on an edge have a range of zero width."""
+    rng = np.random.default_rng(77)
+    dt, w, hw = 1.0 / 256.0, 5, 2
+    traces = [rng.standard_normal(8), rng.standard_normal(20), rng.standard_normal(20),
+              rng.standard_normal(20)]
+    h = [16.0, 8.0, 0.0, 12.0]
+    ds = dataset(traces, h, dt, out_ns=[10])
+    C = np.float32([2.0 ** -20, 1.5 * 2.0 ** -20])
+    r = oracle.cmp_semblance(ds, C, w=w)
+    f = [np.asarray(t, np.float32).astype(np.float64) for t in traces]
+
+    def win(i, u):
+        return [float(np.interp(u + j, np.arange(len(f[i])), f[i])) for j in range(-hw, hw + 1)]
+
+    def inside(i, u):
+        k = np.floor(u)
+        return k - hw >= 0 and k + hw + 1 <= len(f[i]) - 1
+
+    for n, edge_tr in ((3, 0), (0, 1)):
+        us = [np.sqrt(n * n + 2.0 ** -20 * hh * hh / dt ** 2) for hh in h]
+        assert us[edge_tr] == (5.0 if n == 3 else 2.0)
+        base = [win(i, us[i]) for i in range(4) if i != edge_tr and inside(i, us[i])]
+        outcomes = [_window_S(base, w), _window_S(base + [win(edge_tr, us[edge_tr])], w)]
+        Ss = [o[0] for o in outcomes]
+        sts = [o[1] for o in outcomes]
+        assert r.edge[n, 0] == 1
+        assert r.S_lo[n, 0] == pytest.approx(min(Ss), abs=1e-14)
+        assert r.S_hi[n, 0] == pytest.approx(max(Ss), abs=1e-14)
+        assert r.st_lo[n, 0] == pytest.approx(min(sts), abs=1e-14)
+        assert r.st_hi[n, 0] == pytest.approx(max(sts), abs=1e-14)
+        assert (r.N_lo[n, 0], r.N_hi[n, 0]) == (len(base), len(base) + 1)
+        # the nominal (exact-arithmetic) result is the outcome u itself gives
+        nominal = 1 if inside(edge_tr, us[edge_tr]) else 0
+        assert r.S[n, 0] == pytest.approx(Ss[nominal], abs=1e-14)
+        assert abs(max(Ss) - min(Ss)) > 1e-3            # the edge matters here
+    plain = r.edge == 0
+    assert plain.sum() >= 15
+    np.testing.assert_array_equal(r.S_lo[plain], r.S[plain])
+    np.testing.assert_array_equal(r.S_hi[plain], r.S[plain])
+    np.testing.assert_array_equal(r.st_lo[plain], r.stack_at[plain])
+    np.testing.assert_array_equal(r.stack_at[np.arange(10), r.best_idx], r.stack)
+
+
+def test_admissible_range_t0win_bruteforce():
+    """t0-window semblance (w = 3) at row 3: at t0' = 3 dt trace 0 (6 samples, h = 16 m)
+    meets u = 5 exactly, out in exact arithmetic (k + 1 = 6 > 5) but in at k = 4, x = 1 for
+    u a hair below 5; its other window rows are not on an edge.  The range is the min / max
+    of the two outcomes (brute force)."""
+    rng = np.random.default_rng(78)
+    dt, w = 1.0 / 256.0, 3
+    traces = [rng.standard_normal(6), rng.standard_normal(20), rng.standard_normal(20)]
+    h = [16.0, 0.0, 10.0]
+    ds = dataset(traces, h, dt, out_ns=[8])
+    C = np.float32([2.0 ** -20])
+    r = oracle.cmp_semblance(ds, C, w=w, t0_window=True)
+    f = [np.asarray(t, np.float32).astype(np.float64) for t in traces]
+    n = 3
+
+    def S_of(force_in):
+        s, e, M = [], [], []
+        for n2 in (n - 1, n, n + 1):
+            vals = []
+            for i in range(3):
+                u = np.sqrt(n2 * n2 + 2.0 ** -20 * h[i] ** 2 / dt ** 2)
+                ok = np.floor(u) >= 0 and np.floor(u) + 1 <= len(f[i]) - 1
+                if i == 0 and n2 == n:
+                    assert u == 5.0 and not ok
+                    ok = force_in
+                if ok:
+                    vals.append(float(np.interp(min(u, len(f[i]) - 1), np.arange(len(f[i])), f[i])))
+            s.append(sum(vals)); e.append(sum(v * v for v in vals)); M.append(len(vals))
+        den = sum(m * x for m, x in zip(M, e))
+        return sum(x * x for x in s) / den, s[1] / M[1]
+
+    outs = [S_of(False), S_of(True)]
+    assert r.edge[n, 0] == 1
+    assert r.S_lo[n, 0] == pytest.approx(min(o[0] for o in outs), abs=1e-14)
+    assert r.S_hi[n, 0] == pytest.approx(max(o[0] for o in outs), abs=1e-14)
+    assert r.st_lo[n, 0] == pytest.approx(min(o[1] for o in outs), abs=1e-14)
+    assert r.st_hi[n, 0] == pytest.approx(max(o[1] for o in outs), abs=1e-14)
+    assert r.S[n, 0] == pytest.approx(outs[0][0], abs=1e-14)
