@@ -134,6 +134,22 @@ int seis_autotune_save(const char* path);
 int seis_autotune_load(const char* path);
 int seis_autotune_clear(void);
 
+/* Candidate grid of the CMP search -- Section 3.2 (the NMO velocity array is generated
+ * from its lower and upper bounds): nc velocities linearly spaced over [vmin, vmax] m/s,
+ * both bounds included (nc = 1 gives vmin alone), written as C = 4/v^2 (s^2/m^2), the
+ * parameter of the hyperbola t^2 = t0^2 + C h^2 in half-offset h (Section 2.1).  Each value
+ * is formed in FP64 and rounded once to FP32.
+ *   C_out [nc] device, caller-owned.  Asynchronous, one launch.
+ * Errors: SEIS_EINVAL (C_out NULL, nc < 1, a bound not finite or not positive), SEIS_ECUDA. */
+int seis_velocity_grid(double vmin, double vmax, int32_t nc, float* C_out, void* stream);
+
+/* A linear parameter axis: n values lo + (hi - lo) i / (n - 1), i = 0 .. n-1, both ends
+ * included (n = 1 gives lo), formed in FP64 and rounded once to FP32 -- the A, B and C axes
+ * of the CRS search (Section 2.2; the flattened grid of crs_semblance).
+ *   out [n] device, caller-owned.  Asynchronous, one launch.
+ * Errors: SEIS_EINVAL (out NULL, n < 1, a bound not finite), SEIS_ECUDA. */
+int seis_linear_grid(double lo, double hi, int32_t n, float* out, void* stream);
+
 /* CMP semblance search -- Section 2.1, Eq. 1, Algorithm 1, Section 3.2.
  * For every output row (gather g, t0 = n*dt[g]) and every candidate C[c] (C = 4/v^2,
  * s^2/m^2) each trace of gather g is intersected at t = sqrt(t0^2 + C h^2), its

@@ -99,6 +99,8 @@ def load_library(path: str | None = None):
             lib.seis_batch_semblance.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, i32,
                                                  vp, vp, vp, vp, i64, vp, ctypes.c_size_t, vp]
             lib.seis_selftest_wait_timeout.argtypes = [i32, vp]
+            lib.seis_velocity_grid.argtypes = [ctypes.c_double, ctypes.c_double, i32, vp, vp]
+            lib.seis_linear_grid.argtypes = [ctypes.c_double, ctypes.c_double, i32, vp, vp]
             lib.seis_autotune_batch.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, vp,
                                                 vp, vp, vp, i64, vp, ctypes.c_size_t, i32, vp,
                                                 vp, vp]
@@ -112,7 +114,7 @@ def load_library(path: str | None = None):
                          "crs_semblance_grad", "crs_refine", "crs_top_starts",
                          "crs_refine_multi", "seis_batch_semblance", "seis_autotune_batch",
                          "seis_crs_aperture_offset", "crs_pragmatic", "cmp_semblance_t0win",
-                         "crs_semblance_t0win",
+                         "crs_semblance_t0win", "seis_velocity_grid", "seis_linear_grid",
                          "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -253,16 +255,24 @@ def to_device(ds: dict, device="cuda", non_blocking=False) -> Gathers:
                    rows=int(out_off[-1]))
 
 
-def velocity_grid(vmin: float, vmax: float, nc: int, device="cuda") -> torch.Tensor:
-    """Candidate grid of Section 3.2: nc velocities linearly spaced in [vmin, vmax]
-    (bounds included), as C = 4/v^2 in FP32."""
-    v = np.linspace(vmin, vmax, nc, dtype=np.float64) if nc > 1 else np.array([vmin], np.float64)
-    return torch.from_numpy((4.0 / v ** 2).astype(np.float32)).to(device)
+def velocity_grid(vmin: float, vmax: float, nc: int, device="cuda", stream=None) -> torch.Tensor:
+    """Candidate grid of Section 3.2, C = 4/v^2 for nc velocities linearly spaced over
+    [vmin, vmax] (include/seis.h: seis_velocity_grid), as a device tensor."""
+    lib = load_library()
+    out = torch.empty(int(nc), dtype=torch.float32, device=device)
+    _check(lib.seis_velocity_grid(ctypes.c_double(vmin), ctypes.c_double(vmax), int(nc),
+                                  _ptr(out), _stream_handle(stream)))
+    return out
 
 
-def linear_grid(lo: float, hi: float, n: int, device="cuda") -> torch.Tensor:
-    g = np.linspace(lo, hi, n, dtype=np.float64) if n > 1 else np.array([lo], np.float64)
-    return torch.from_numpy(g.astype(np.float32)).to(device)
+def linear_grid(lo: float, hi: float, n: int, device="cuda", stream=None) -> torch.Tensor:
+    """A linear CRS parameter axis of n values over [lo, hi] (include/seis.h:
+    seis_linear_grid), as a device tensor."""
+    lib = load_library()
+    out = torch.empty(int(n), dtype=torch.float32, device=device)
+    _check(lib.seis_linear_grid(ctypes.c_double(lo), ctypes.c_double(hi), int(n), _ptr(out),
+                                _stream_handle(stream)))
+    return out
 
 
 def cmp_semblance(g: Gathers, C: torch.Tensor, w: int = 11, want_cube: bool = False,
@@ -360,14 +370,17 @@ def crs_aperture(g: Gathers, central, apm: float, hmax: float | None = None,
     return Aperture(nbr_off, nbr_trace, m_c, out_off, dt_c, n, int(mr.value), int(rows.value))
 
 
-def _crs_search(lib_fn, g, ap, A, B, C, w, want_cube, stream) -> dict:
+def _crs_search(lib_fn, g, ap, A, B, C, w, want_cube, stream, out=None) -> dict:
     lib = load_library()
     dev = g.traces.device
     A, B, C = _input(A, "A", dev), _input(B, "B", dev), _input(C, "C", dev)
     nA, nB, nC = int(A.numel()), int(B.numel()), int(C.numel())
-    out = _rows_out(dev, ap.rows, abc=True)
-    if want_cube:
-        out["S"] = torch.empty((ap.rows, nA * nB * nC), dtype=torch.float32, device=dev)
+    if out is None:
+        out = _rows_out(dev, ap.rows, abc=True)
+        if want_cube:
+            out["S"] = torch.empty((ap.rows, nA * nB * nC), dtype=torch.float32, device=dev)
+    else:
+        _check_rows_out(out, dev, ap.rows, nA * nB * nC, abc=True)
     rc = getattr(lib, lib_fn)(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
                               _ptr(A), nA, _ptr(B), nB, _ptr(C), nC, w, _ptr(out.get("S")),
                               _ptr(out["best_idx"]), _ptr(out["best_ABC"]), _ptr(out["best_S"]),
@@ -377,10 +390,11 @@ def _crs_search(lib_fn, g, ap, A, B, C, w, want_cube, stream) -> dict:
 
 
 def crs_semblance(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor,
-                  w: int = 11, want_cube: bool = False, stream=None) -> dict:
+                  w: int = 11, want_cube: bool = False, stream=None, out: dict | None = None) -> dict:
     """CRS semblance search over the flattened A x B x C grid (include/seis.h:
-    crs_semblance).  Returns best_idx, best_ABC [rows, 3], best_S, stack (and S)."""
-    return _crs_search("crs_semblance", g, ap, A, B, C, w, want_cube, stream)
+    crs_semblance).  Returns best_idx, best_ABC [rows, 3], best_S, stack (and S); `out`
+    supplies the output tensors instead (as cmp_semblance)."""
+    return _crs_search("crs_semblance", g, ap, A, B, C, w, want_cube, stream, out)
 
 
 def crs_semblance_t0win(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor,

@@ -36,8 +36,7 @@ def _check_all(seis, ds, C, w=11, label="", max_exempt=parity.MAX_EXEMPT_SMALL):
     got = _run(seis, ds, C, w)
     ref = oracle.cmp_semblance(ds, C, w=w)
     rep = parity.check_cube(got["S"], ref, label, max_exempt=max_exempt)
-    rep.update(parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, label,
-                                  edge=ref.edge))
+    rep.update(parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, label))
     np.testing.assert_array_equal(got["best_C"], C[got["best_idx"]])
     return got, ref, rep
 
@@ -126,8 +125,7 @@ def test_cmp_line_full_size_sampled(seis):
     rows = np.concatenate([rows, [0, 1999, 2000, 8191999]])
     ref = oracle.cmp_semblance(ds, C, rows=rows)
     sub = {k: got[k][rows] for k in ("best_idx", "best_S", "stack")}
-    rep = parity.check_picks(sub["best_idx"], sub["best_S"], sub["stack"], ref, "cmp-line",
-                             edge=ref.edge)
+    rep = parity.check_picks(sub["best_idx"], sub["best_S"], sub["stack"], ref, "cmp-line")
     assert rep["pick_agree"] > 0.98
     assert np.all(got["best_S"] >= 0) and np.all(got["best_S"] <= 1.0 + 1e-5)
 
@@ -139,10 +137,10 @@ def test_paper_table1_shapes(seis, shape):
     fold, ns = synth.PAPER_SHAPES[shape]
     ds = synth.cmp_line(2, fold, ns, 0.004, 25.0, 3000.0, 4, 1.0, seed=300 + fold + ns,
                         v_range=(2550.0, 3450.0))
-    # a (row, candidate) is exempt when any of its traces sits on a mask edge within 1e-3
-    # samples, so the exempt fraction grows with the fold (about 5e-3 at fold 1000)
-    _check_all(seis, ds, _grid(23), label=f"cmp {shape}",
-               max_exempt=parity.MAX_EXEMPT_SMALL if fold < 1000 else 2e-2)
+    # an entry has a flagged trace when any of its traces sits on a mask edge within 1e-3
+    # samples (about 5e-3 of the entries at fold 1000); the oracle resolves every such entry
+    # into its admissible range, so no entry is left unchecked
+    _check_all(seis, ds, _grid(23), label=f"cmp {shape}", max_exempt=parity.MAX_EXEMPT)
 
 
 # --- t0-window semblance (window over neighbouring output times) -------------------------
@@ -155,8 +153,7 @@ def _check_t0win(seis, ds, C, w, label, max_exempt=parity.MAX_EXEMPT_SMALL):
     got = {k: v.cpu().numpy() for k, v in out.items()}
     ref = oracle.cmp_semblance(ds, C, w=w, t0_window=True)
     parity.check_cube(got["S"], ref, label, max_exempt=max_exempt)
-    rep = parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, label,
-                             edge=ref.edge)
+    rep = parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, label)
     np.testing.assert_array_equal(got["best_C"], C[got["best_idx"]])
     return rep
 
@@ -182,10 +179,11 @@ def test_t0win_ragged_traces(seis):
 
 def test_t0win_cmp_small_workload(seis):
     ds = synth.workload_cmp_small()
-    # an entry is exempt when any trace at any of the w output times of its window sits on
-    # a mask edge, so about w times as many entries are exempt as for the paper's window
+    # an entry has a flagged trace when any trace at any of the w output times of its
+    # window sits on a mask edge (about w times as often as for the paper's window); the
+    # oracle resolves each into its admissible range
     rep = _check_t0win(seis, ds, _grid(101), 11, "t0win cmp-small",
-                       max_exempt=11 * parity.MAX_EXEMPT)
+                       max_exempt=parity.MAX_EXEMPT)
     assert rep["pick_agree"] > 0.99
 
 
@@ -213,3 +211,26 @@ def test_t0win_ragged_gathers_empty_and_fold_one(seis):
     one = slice(o[2], o[3])
     live = ref.S[one] > 0
     np.testing.assert_allclose(S[one][live], 1.0, atol=1e-6)
+
+
+# --- candidate grids (Section 3.2) ----------------------------------------------------
+
+@pytest.mark.parametrize("vmin,vmax,nc", [(1400.0, 4500.0, 201), (1400.0, 4500.0, 101),
+                                          (1500.0, 1500.0, 3), (2000.0, 3000.0, 1),
+                                          (4500.0, 1400.0, 37)])
+def test_velocity_grid_matches_oracle(seis, vmin, vmax, nc):
+    """The library's C = 4/v^2 grid equals the oracle's FP64 grid rounded to FP32, bit for
+    bit."""
+    got = seis.velocity_grid(vmin, vmax, nc).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.velocity_grid(vmin, vmax, nc).astype(np.float32))
+
+
+def test_linear_grids_match_oracle(seis):
+    for lo, hi in synth.crs_ranges():
+        for n in (1, 7, 11, 21, 41, 81):
+            got = seis.linear_grid(lo, hi, n).cpu().numpy()
+            np.testing.assert_array_equal(got, oracle.linear_grid(lo, hi, n).astype(np.float32))
+    with pytest.raises(seis.SeisError):
+        seis.velocity_grid(0.0, 4500.0, 5)
+    with pytest.raises(seis.SeisError):
+        seis.linear_grid(0.0, 1.0, 0)
