@@ -57,9 +57,11 @@ def _intersections(ds, nc):
     return int(np.sum(fold.astype(np.int64) * rows.astype(np.int64)) * nc)
 
 
-def _candidates():
-    v = np.linspace(VMIN, VMAX, NC)
-    return (4.0 / v ** 2).astype(np.float32)
+def _candidates(seis, dev):
+    """The 201 candidates C = 4/v^2 (v in 1400..4500 m/s), from the library's grid entry
+    point: a device tensor and its host copy."""
+    Cd = seis.velocity_grid(VMIN, VMAX, NC, device=dev)
+    return Cd, Cd.cpu().numpy()
 
 
 def _cpu_info():
@@ -247,10 +249,9 @@ def _max_over_ranks(torch, dist, world, dev, x):
 
 def run_cmp_line(args, torch, dist, seis, synth, rank, world, dev):
     ds = synth.workload_cmp_line(seed=2 + 1000 * rank, G=args.gathers)
-    C = _candidates()
+    Cd, C = _candidates(seis, dev)
     inter = _intersections(ds, NC)
     g = seis.to_device(ds, dev)
-    Cd = torch.from_numpy(C).to(dev)
     # autotune on a slice in the same shape bucket (same fold, rows, candidates)
     if args.variant is None:
         sub = synth.cmp_line(min(512, args.gathers), 60, 2000, 0.004, 25.0, 3000.0, 8, 1.0,
@@ -414,10 +415,11 @@ def _e2e(args, ds, C, g, Cd, out, inter, world, dev, stream, torch, dist, seis):
 
 # ------------------------------------------------------------------ the other workloads ----
 
-def _crs_grids(torch, dev, synth, nA, nB, nC):
+def _crs_grids(seis, dev, synth, nA, nB, nC):
+    """The CRS A, B, C axes over the ranges of the synthetic model (library grid entry point)."""
     (alo, ahi), (blo, bhi), (clo, chi) = synth.crs_ranges()
-    f = lambda lo, hi, n: torch.from_numpy(np.linspace(lo, hi, n).astype(np.float32)).to(dev)
-    return f(alo, ahi, nA), f(blo, bhi, nB), f(clo, chi, nC)
+    return (seis.linear_grid(alo, ahi, nA, device=dev), seis.linear_grid(blo, bhi, nB, device=dev),
+            seis.linear_grid(clo, chi, nC, device=dev))
 
 
 def _simple_line(metric, value, ms, args, world, config, extra=None, clk=None, launches=None):
@@ -435,7 +437,7 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
     g = seis.to_device(ds, dev)
     central = ds["central"][:args.centrals]
     ap = seis.crs_aperture(g, central, ds["apm"])
-    A, B, C = _crs_grids(torch, dev, synth, 21, 21, 41)
+    A, B, C = _crs_grids(seis, dev, synth, 21, 21, 41)
     inter = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 1500 * 21 * 21 * 41
     # autotune on a 4-central slice in the same shape bucket (candidates, rows, fold)
     if args.variant is None:
@@ -544,35 +546,52 @@ def run_batch(args, torch, dist, seis, synth, rank, world, dev):
 
 
 def run_refine(args, torch, dist, seis, synth, rank, world, dev):
+    """Coarse 7x7x11 search, its nstart best candidates per row as starts, 20 projected BFGS
+    steps from each (adjoint kernel), best kept -- against the dense 41x41x81 search timed on
+    whole waves of CTAs.  Each part is timed with CUDA events on the launching stream."""
     ds = synth.workload_crs_refine(seed=5 + 1000 * rank)
     g = seis.to_device(ds, dev)
-    ap = seis.crs_aperture(g, ds["central"], ds["apm"])
+    central = ds["central"][:args.centrals]          # all 512 unless profiling a slice
+    ap = seis.crs_aperture(g, central, ds["apm"])
     (alo, ahi), (blo, bhi), (clo, chi) = synth.crs_ranges()
     lo, hi = [alo, blo, clo], [ahi, bhi, chi]
-    A7, B7, C11 = _crs_grids(torch, dev, synth, 7, 7, 11)
+    A7, B7, C11 = _crs_grids(seis, dev, synth, 7, 7, 11)
     nstart, steps = args.starts, 20
     ws = torch.empty(seis.load_library().seis_refine_multi_workspace_size(ap.rows) + 256,
                      dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    marks = []
 
-    def refine_all():
+    def refine_all(record=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)] if record else None
         coarse = seis.crs_semblance(g, ap, A7, B7, C11, w=W, want_cube=True)
         starts = seis.crs_top_starts(coarse["S"], A7, B7, C11, nstart)
-        return coarse, seis.crs_refine_multi(g, ap, starts, lo, hi, steps=steps, step0=0.05,
-                                             w=W, workspace=ws)
+        if record:
+            ev[0].record(stream)
+        ref = seis.crs_refine_multi(g, ap, starts, lo, hi, steps=steps, step0=0.05, w=W,
+                                    workspace=ws)
+        if record:
+            ev[1].record(stream)
+            marks.append(ev)
+        return coarse, ref
     for _ in range(args.warmup):
         refine_all()
     torch.cuda.synchronize()
+    seis.device_status()
     clocks = ClockSampler(dev.index)
     clocks.start()
-    _, total = _time_steps(torch, torch.cuda.current_stream(), refine_all, args.steps)
+    kern, total = _time_steps(torch, stream, lambda: refine_all(record=True), args.steps)
     clk = clocks.stop()
+    seis.device_status()
     refine_ms = total / args.steps
+    multi_ms = float(np.mean([a.elapsed_time(b) for a, b in marks]))
+    search_ms = float(np.mean(kern)) - multi_ms       # coarse search + start selection
     coarse, ref = refine_all()
     one = seis.crs_refine(g, ap, coarse["best_ABC"], lo, hi, steps=steps, step0=0.05, w=W)
     # the dense 41x41x81 search on a slice of centrals, timed and extrapolated
-    nd = args.dense_centrals
-    apd = seis.crs_aperture(g, ds["central"][:nd], ds["apm"])
-    A41, B41, C81 = _crs_grids(torch, dev, synth, 41, 41, 81)
+    nd = min(args.dense_centrals, len(central))
+    apd = seis.crs_aperture(g, central[:nd], ds["apm"])
+    A41, B41, C81 = _crs_grids(seis, dev, synth, 41, 41, 81)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -582,7 +601,7 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
     torch.cuda.synchronize()
     seis.device_status()
     dense_ms_slice = e0.elapsed_time(e1)
-    dense_ms = dense_ms_slice * len(ds["central"]) / nd
+    dense_ms = dense_ms_slice * len(central) / nd
     rows_d = apd.rows
     S_dense = dense["best_S"].cpu().numpy()
     bins = [0.0, 0.005, 0.02, 0.1, 1.01]
@@ -597,22 +616,41 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
         return {"rows_within_1e-3_of_dense": float(ok.mean()),
                 "rows_above_dense": float(np.mean(gap < 0)),
                 "median_S_refined_minus_dense": float(np.median(-gap)), "by_S_dense": per}
-    nrows_inter = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 2000
-    inter_refine = nrows_inter * (539 + nstart * (steps + 1))
+    trace_rows = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 2000
+    inter_coarse = trace_rows * 539
+    inter_eval = trace_rows * nstart * (steps + 1)
+    inter_refine = inter_coarse + inter_eval
     launches = 2 + nstart * (2 * steps + 3)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    flops_eval = FLOPS_PER_INTERSECTION + 8 * W      # evaluation + adjoint (4 FMAs per sample)
+    ach_eval = inter_eval * flops_eval / (multi_ms / 1e3) / 1e12
+    ach_search = inter_coarse * FLOPS_PER_INTERSECTION / (search_ms / 1e3) / 1e12
     return _simple_line("CRS refine " + METRIC, inter_refine * W / (refine_ms / 1e3), refine_ms,
                         args, world,
-                        {"workload": "refine: 512 central CMPs, aperture +-8 CMPs (816 traces), "
+                        {"workload": f"refine: {len(central)} central CMPs of 512, aperture +-8 "
+                                     "CMPs (816 traces), "
                                      f"2000 samples @4ms; coarse 7x7x11, its {nstart} best "
                                      f"candidates per row each refined by {steps} projected "
                                      "BFGS gradient-ascent steps, best kept; vs dense 41x41x81",
-                         "starts": nstart, "steps": steps, "dense_centrals_timed": nd},
-                        {"refine_ms": refine_ms, "dense_ms_extrapolated": dense_ms,
-                         "dense_ms_slice": dense_ms_slice,
+                         "starts": nstart, "steps": steps, "dense_centrals_timed": nd,
+                         "dense_ctas": int(nd * ((2000 + 31) // 32)),
+                         "resident_cta_slots": 2 * sms},
+                        {"refine_ms": refine_ms, "coarse_search_ms": search_ms,
+                         "refine_multi_ms": multi_ms,
+                         "dense_ms_extrapolated": dense_ms, "dense_ms_slice": dense_ms_slice,
                          "speedup_refine_vs_dense": dense_ms / refine_ms,
                          **quality(ref["S"]),
                          "one_start (untimed, for comparison)": quality(one["S"]),
-                         "mean_S_gain_over_coarse": float((ref["S"] - coarse["best_S"]).mean())},
+                         "mean_S_gain_over_coarse": float((ref["S"] - coarse["best_S"]).mean()),
+                         "roofline": {"bound": "alu", "kernel": "eval_kernel<CRS, w=11, adjoint>",
+                                      "achieved": ach_eval, "peak": peak, "unit": "TFLOP/s",
+                                      "frac": ach_eval / peak, "traffic": None,
+                                      "flops_per_evaluation": flops_eval,
+                                      "evaluation_intersections_per_step": inter_eval,
+                                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x "
+                                                    f"{SM_MAX_MHZ:g} MHz",
+                                      "coarse_search_frac": ach_search / peak}},
                         clk, launches)
 
 
@@ -620,10 +658,9 @@ def run_t0win(args, torch, dist, seis, synth, rank, world, dev):
     """The window over neighbouring output times (one interpolation per intersection)
     against the paper's window along each trace, on the cmp-line workload."""
     ds = synth.workload_cmp_line(seed=2 + 1000 * rank, G=args.gathers)
-    C = _candidates()
+    Cd, C = _candidates(seis, dev)
     inter = _intersections(ds, NC)
     g = seis.to_device(ds, dev)
-    Cd = torch.from_numpy(C).to(dev)
     stream = torch.cuda.current_stream()
     # the paper's window runs with the variant the autotuner picks for this shape
     sub = synth.cmp_line(min(512, args.gathers), 60, 2000, 0.004, 25.0, 3000.0, 8, 1.0,
@@ -655,7 +692,7 @@ def run_t0win(args, torch, dist, seis, synth, rank, world, dev):
     dc = synth.workload_crs_line(seed=3 + 1000 * rank)
     gc = seis.to_device(dc, dev)
     ap = seis.crs_aperture(gc, dc["central"][:64], dc["apm"])
-    A, B, Cc = _crs_grids(torch, dev, synth, 21, 21, 41)
+    A, B, Cc = _crs_grids(seis, dev, synth, 21, 21, 41)
     apt = seis.crs_aperture(gc, dc["central"][:4], dc["apm"])
     seis.autotune_crs(gc, apt, A, B, Cc, w=W, reps=1)
     seis.crs_semblance_t0win(gc, ap, A, B, Cc, w=W)
@@ -694,7 +731,7 @@ def run_pragmatic(args, torch, dist, seis, synth, rank, world, dev):
     ap_z = seis.crs_aperture(g, central, ds["apm"], hmax=0.0)
     (alo, ahi), (blo, bhi), _ = synth.crs_ranges()
     lo, hi = [alo, blo, synth.crs_ranges()[2][0]], [ahi, bhi, synth.crs_ranges()[2][1]]
-    A, B, C = _crs_grids(torch, dev, synth, 21, 21, 41)
+    A, B, C = _crs_grids(seis, dev, synth, 21, 21, 41)
     ws = torch.empty(seis.load_library().seis_pragmatic_workspace_size(ap.rows) + 256,
                      dtype=torch.uint8, device=dev)
     prag = lambda: seis.crs_pragmatic(g, ap, ap_c, ap_z, A, B, C, float(C[0]), w=W, workspace=ws)
@@ -756,9 +793,8 @@ PAPER_RUNS = [("data1/data2", 8192, 64, 10), ("data3/data4", 2048, 17, 10),
 
 
 def run_paper(args, torch, dist, seis, synth, rank, world, dev):
-    C = _candidates()
-    Cd = torch.from_numpy(C).to(dev)
-    A, B, Cc = _crs_grids(torch, dev, synth, 21, 21, 41)
+    Cd, C = _candidates(seis, dev)
+    A, B, Cc = _crs_grids(seis, dev, synth, 21, 21, 41)
     ncrs = 21 * 21 * 41
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -842,6 +878,17 @@ def run_ours(args):
           "refine": run_refine, "paper": run_paper, "pragmatic": run_pragmatic,
           "t0win": run_t0win}[args.workload]
     line = fn(args, torch, dist, seis, synth, rank, world, dev)
+    if args.workload == "cmp-line" and world == 1 and not args.no_secondary:
+        # the CRS search and the refinement, each with its own CUDA-event time, roofline and
+        # clock record, beside the CMP headline (short runs: 1 warm-up, 2 timed steps)
+        for key, sub_fn, extra in (("crs", run_crs_line, {"centrals": 64}), ("refine", run_refine, {})):
+            sub_args = argparse.Namespace(**{**vars(args), "steps": 2, "warmup": 1,
+                                             "no_cpu_baseline": True, "variant": None, **extra})
+            sub = sub_fn(sub_args, torch, dist, seis, synth, rank, world, dev)
+            for k in ("n_gpus", "vs_baseline", "data", "e2e", "higher_is_better", "scaling",
+                      "dtype", "cpu_baseline"):
+                sub.pop(k, None)
+            line[key] = sub
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -853,15 +900,17 @@ def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
         return
+    import oracle
     from paper_1907_11678_gb300 import synth
     ds = synth.workload_cmp_line()
-    C = _candidates()
-    vals = []
+    C = oracle.velocity_grid(VMIN, VMAX, NC).astype(np.float32)
+    vals, secs = [], []
     info = None
     for i in range(args.warmup + args.steps):
         v, info = oracle_baseline(ds, C, target_s=args.ref_seconds, seed=i)
         if i >= args.warmup:
             vals.append(v)
+            secs.append(info["seconds"])
     value = float(np.mean(vals))
     inter_per_row = NC * 60
     line = {
@@ -872,7 +921,12 @@ def run_reference(args):
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": 1e3 * 4096 * 2000 * inter_per_row * W / value,
+        # a step is one bounded sample of the workload (the oracle on seeded rows), timed
+        "ms_per_step": 1e3 * float(np.mean(secs)),
+        "step": "one seeded sample of output rows of the cmp-line workload (all candidates and "
+                "traces of each row), about --ref-seconds of oracle work, wall clock",
+        "projected_full_line_ms (projection, not measured)":
+            1e3 * 4096 * 2000 * inter_per_row * W / value,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -909,6 +963,8 @@ def main():
                     help="refine: dense-grid slice (24 x 63 tiles = 4.97 waves of 304 CTAs)")
     ap.add_argument("--starts", type=int, default=16, help="refine: coarse starts per row")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="cmp-line: leave out the crs and refine sub-objects")
     ap.add_argument("--variant", type=int, default=None,
                     help="force a search kernel variant instead of autotuning (profiling)")
     args = ap.parse_args()

@@ -33,6 +33,8 @@ def test_reference_arm_prints_one_contract_line():
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("cmp-line: 4096 gathers")
     assert d["gpu_launches"] == 0
+    # a step is one measured sample (about --ref-seconds of oracle work), not a projection
+    assert 0 < d["ms_per_step"] < 60000
 
 
 def test_reference_arm_other_ranks_exit_without_work():
