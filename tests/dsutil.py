@@ -43,3 +43,20 @@ def pythagorean_offsets(n0, max_leg, scale=4):
         if r * r == mm:
             out.append((a, r))
     return out
+
+
+def ragged_line(ds, seed, trim=40, row_trim=30):
+    """A copy of a uniform line (synth.crs_line) whose traces are cut to random lengths
+    (up to `trim` samples shorter) and whose gathers have random output row counts (up to
+    `row_trim` rows fewer): gathers of uneven trace length and rows."""
+    rng = np.random.default_rng(seed)
+    toff = np.asarray(ds["trace_off"], np.int64)
+    n = len(toff) - 1
+    lens = np.diff(toff)
+    keep = lens - rng.integers(0, trim + 1, n)
+    traces = np.concatenate([ds["traces"][toff[i]:toff[i] + keep[i]] for i in range(n)])
+    ooff = np.asarray(ds["out_off"], np.int64)
+    rows = np.diff(ooff) - rng.integers(0, row_trim + 1, len(ooff) - 1)
+    return dict(ds, traces=traces.astype(np.float32),
+                trace_off=np.concatenate([[0], np.cumsum(keep)]).astype(np.int64),
+                out_off=np.concatenate([[0], np.cumsum(rows)]).astype(np.int64))

@@ -40,37 +40,32 @@ def _worker(rank, world, port, q):
     import torch.distributed as dist
     import oracle
     from paper_1907_11678_gb300 import synth
+    from tests.dsutil import ragged_line
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         n_cdp, halo = 24, 3
-        full = synth.crs_line(n_cdp, 6, 260, 0.004, 0.0, 1200.0, 2, 1, 2.0, seed=17)
+        full = ragged_line(synth.crs_line(n_cdp, 6, 260, 0.004, 0.0, 1200.0, 2, 1, 2.0, seed=17),
+                           seed=5)
         (ob, oe), (nb, ne) = sdist.crs_partition(n_cdp, world, rank, halo)
-        # this rank's owned gathers only
-        t0, t1 = int(full["gather_off"][ob]), int(full["gather_off"][oe])
-        s0, s1 = int(full["trace_off"][t0]), int(full["trace_off"][t1])
-        local = dict(traces=full["traces"][s0:s1], trace_off=full["trace_off"][t0:t1 + 1] - s0,
-                     h=full["h"][t0:t1], m=full["m"][t0:t1],
-                     gather_off=full["gather_off"][ob:oe + 1] - t0,
-                     out_off=full["out_off"][ob:oe + 1] - full["out_off"][ob],
-                     dt=full["dt"][ob:oe])
+        local = sdist.local_part(full, ob, oe)              # this rank's owned gathers only
         ext = sdist.exchange_halos(local, n_cdp, halo, rank, world)
-        assert len(ext["gather_off"]) - 1 == ne - nb
+        # the extended line is exactly the global gathers [nb, ne)
+        want = sdist.local_part(full, nb, ne)
+        same = all(np.array_equal(ext[k], want[k]) for k in
+                   ("traces", "trace_off", "h", "m", "gather_off", "out_off", "dt"))
         apm = halo * 12.5
         A = np.float32([-2e-4, 0.0, 2e-4]); B = np.float32([0.0, 1e-6]); C = np.float32([3e-7, 8e-7, 1.5e-6])
         central_local = np.arange(ob - nb, oe - nb, dtype=np.int32)
-        off, tr, mc = oracle.neighbours(ext, central_local, apm)
-        nb_loc = (off, tr, mc, np.arange(len(central_local) + 1, dtype=np.int64) * 260,
-                  np.float32([0.004] * len(central_local)))
+        nb_loc = oracle.aperture(ext, central_local, apm)
         mine = oracle.crs_semblance(ext, nb_loc, A, B, C, want_cube=True)
         # single-process reference for the same centrals
-        off2, tr2, mc2 = oracle.neighbours(full, np.arange(ob, oe, dtype=np.int32), apm)
-        nb_full = (off2, tr2, mc2, np.arange(oe - ob + 1, dtype=np.int64) * 260,
-                   np.float32([0.004] * (oe - ob)))
+        nb_full = oracle.aperture(full, np.arange(ob, oe, dtype=np.int32), apm)
         ref = oracle.crs_semblance(full, nb_full, A, B, C, want_cube=True)
-        ok = (np.array_equal(np.diff(off), np.diff(off2)) and np.array_equal(mine.S, ref.S)
-              and np.array_equal(mine.best_idx, ref.best_idx) and np.array_equal(mine.stack, ref.stack))
+        ok = (same and np.array_equal(np.diff(nb_loc[0]), np.diff(nb_full[0]))
+              and np.array_equal(mine.S, ref.S) and np.array_equal(mine.best_idx, ref.best_idx)
+              and np.array_equal(mine.stack, ref.stack))
         t = sdist.max_over_ranks(float(rank) + 0.5)
         q.put((rank, ok, t))
     finally:
@@ -79,6 +74,9 @@ def _worker(rank, world, port, q):
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_crs_halo_exchange_matches_single_process(world):
+    """Ragged line (uneven trace lengths and output rows per gather): every rank's extended
+    line equals the global gathers it needs, and the oracle's CRS search of its central
+    CDPs on it equals the single-process search."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -100,6 +98,8 @@ def test_exchange_halos_single_rank_and_zero_halo():
     ds = synth.crs_line(6, 4, 200, 0.004, 0.0, 500.0, 1, 0, None, seed=12)
     for world, halo in ((1, 3), (1, 0)):
         out = sdist.exchange_halos(ds, 6, halo, 0, world)
+        for k in ("out_off", "dt"):
+            np.testing.assert_array_equal(out[k], ds[k])
         np.testing.assert_array_equal(out["traces"], ds["traces"])
         np.testing.assert_array_equal(out["trace_off"], ds["trace_off"])
         np.testing.assert_array_equal(out["gather_off"], ds["gather_off"])
@@ -113,3 +113,5 @@ def test_exchange_halos_rejects_small_shards():
     ds = synth.crs_line(2, 4, 200, 0.004, 0.0, 500.0, 1, 0, None, seed=13)
     with pytest.raises(ValueError):
         sdist.exchange_halos(ds, 4, 3, 0, 2)
+    with pytest.raises(ValueError):                       # not this rank's share of the line
+        sdist.exchange_halos(ds, 7, 1, 0, 2)
