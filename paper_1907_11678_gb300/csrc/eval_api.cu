@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include "seis.h"
 #include "seis_internal.h"
+#include "eval_pair.h"
 
 namespace seis {
 
@@ -103,13 +104,16 @@ extern "C" size_t seis_refine_workspace_size(int64_t rows) {
 namespace seis {
 
 // The refinement loop of crs_refine on caller-checked arguments: theta [rows][3] in/out,
-// S, grad, stack outputs, ws of seis_refine_workspace_size(rows) bytes (256-aligned).
-int refine_run(const EvalParams& p0, float* theta, const float* lo3, const float* hi3,
-               int32_t steps, float step0, int32_t w, float* S_out, float* grad_out,
-               float* stack_out, void* workspace, int64_t rows, cudaStream_t s) {
-    EvalParams p = p0;
+// S, grad, stack outputs, ws of seis_refine_workspace_size(rows) bytes (256-aligned).  With
+// `pair`, the state holds two starts of the same rows ([2][rows][...]) and each evaluation
+// is one paired launch (eval_pair.cu); the update kernel runs over all 2 rows states.
+static int refine_loop(const EvalParams& p0, float* theta, const float* lo3, const float* hi3,
+                       int32_t steps, float step0, int32_t w, float* S_out, float* grad_out,
+                       float* stack_out, void* workspace, int64_t rows, bool pair,
+                       cudaStream_t s) {
+    const int64_t nstate = pair ? 2 * rows : rows;
     char* ws = static_cast<char*>(workspace);
-    const size_t r = (size_t)rows;
+    const size_t r = (size_t)nstate;
     float* trial_theta = reinterpret_cast<float*>(ws);
     ws += align256(r * 3 * 4);
     float* trial_S = reinterpret_cast<float*>(ws);
@@ -123,7 +127,7 @@ int refine_run(const EvalParams& p0, float* theta, const float* lo3, const float
     float* Hinv = reinterpret_cast<float*>(ws);
 
     RefineParams u{};
-    u.rows = rows;
+    u.rows = nstate;
     u.theta = theta;
     u.S = S_out;
     u.grad = grad_out;
@@ -137,26 +141,50 @@ int refine_run(const EvalParams& p0, float* theta, const float* lo3, const float
     for (int a = 0; a < 3; ++a) { u.lo[a] = lo3[a]; u.hi[a] = hi3[a]; }
     u.step0 = step0;
 
-    // evaluate the starting operators
-    p.theta = theta;
-    p.S = trial_S;
-    p.grad = trial_grad;
-    p.stack = trial_stack;
-    cudaError_t e = launch_eval(p, true, true, w, s);
+    // one evaluation of the operators th into the trial outputs
+    auto evaluate = [&](const float* th) -> cudaError_t {
+        EvalParams p = p0;
+        p.theta = th;
+        p.S = trial_S;
+        p.grad = trial_grad;
+        p.stack = trial_stack;
+        if (!pair) return launch_eval(p, true, true, w, s);
+        EvalPairParams q{};
+        q.p = p;
+        q.theta2 = th + rows * 3;
+        q.S2 = trial_S + rows;
+        q.grad2 = trial_grad + rows * 3;
+        q.stack2 = trial_stack + rows;
+        return launch_eval_pair(q, w, s);
+    };
+    cudaError_t e = evaluate(theta);                   // the starting operators
     if (e != cudaSuccess) return cuda_fail(e, "crs_refine eval");
     u.init = 1;
     u.assess = 0;
     u.propose = steps > 0;
     if ((e = launch_refine_update(u, s)) != cudaSuccess) return cuda_fail(e, "crs_refine update");
     u.init = 0;
-    p.theta = trial_theta;
     for (int it = 0; it < steps; ++it) {
-        if ((e = launch_eval(p, true, true, w, s)) != cudaSuccess) return cuda_fail(e, "crs_refine eval");
+        if ((e = evaluate(trial_theta)) != cudaSuccess) return cuda_fail(e, "crs_refine eval");
         u.assess = 1;
         u.propose = it + 1 < steps;
         if ((e = launch_refine_update(u, s)) != cudaSuccess) return cuda_fail(e, "crs_refine update");
     }
     return SEIS_OK;
+}
+
+int refine_run(const EvalParams& p0, float* theta, const float* lo3, const float* hi3,
+               int32_t steps, float step0, int32_t w, float* S_out, float* grad_out,
+               float* stack_out, void* workspace, int64_t rows, cudaStream_t s) {
+    return refine_loop(p0, theta, lo3, hi3, steps, step0, w, S_out, grad_out, stack_out,
+                       workspace, rows, false, s);
+}
+
+int refine_run_pair(const EvalParams& p0, float* theta, const float* lo3, const float* hi3,
+                    int32_t steps, float step0, int32_t w, float* S_out, float* grad_out,
+                    float* stack_out, void* workspace, int64_t rows, cudaStream_t s) {
+    return refine_loop(p0, theta, lo3, hi3, steps, step0, w, S_out, grad_out, stack_out,
+                       workspace, rows, true, s);
 }
 
 // Argument checks shared by crs_refine and crs_refine_multi.

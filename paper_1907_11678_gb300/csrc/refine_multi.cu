@@ -8,6 +8,7 @@
 #include "seis.h"
 #include "seis_internal.h"
 #include "seis_dev.cuh"
+#include "eval_pair.h"
 
 namespace seis {
 
@@ -100,11 +101,13 @@ extern "C" int crs_top_starts(const float* S_cube, int64_t rows, const float* A,
     return SEIS_OK;
 }
 
+// Starts are refined two at a time (the paired evaluation kernel), so the refinement state
+// and the per-start results hold two starts of every row.
 extern "C" size_t seis_refine_multi_workspace_size(int64_t rows) {
     if (rows < 0) return 0;
-    const size_t r = (size_t)rows;
-    return seis_refine_workspace_size(rows) + align256(r * 3 * 4) + align256(r * 4) +
-           align256(r * 3 * 4) + align256(r * 4);
+    const size_t r2 = 2 * (size_t)rows;
+    return seis_refine_workspace_size(2 * rows) + align256(r2 * 3 * 4) + align256(r2 * 4) +
+           align256(r2 * 3 * 4) + align256(r2 * 4);
 }
 
 extern "C" int crs_refine_multi(const seis_gathers* d, const seis_aperture* ap,
@@ -120,28 +123,35 @@ extern "C" int crs_refine_multi(const seis_gathers* d, const seis_aperture* ap,
                           rows, &p);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t r = (size_t)rows;
+    const size_t r = (size_t)rows, r2 = 2 * r;
     char* ws = static_cast<char*>(workspace);
     void* ws_refine = ws;
-    ws += seis_refine_workspace_size(rows);
-    float* th = reinterpret_cast<float*>(ws);
-    ws += align256(r * 3 * 4);
-    float* S = reinterpret_cast<float*>(ws);
-    ws += align256(r * 4);
+    ws += seis_refine_workspace_size(2 * rows);
+    float* th = reinterpret_cast<float*>(ws);           // [2][rows][3]: starts k and k+1
+    ws += align256(r2 * 3 * 4);
+    float* S = reinterpret_cast<float*>(ws);            // [2][rows]
+    ws += align256(r2 * 4);
     float* g = reinterpret_cast<float*>(ws);
-    ws += align256(r * 3 * 4);
+    ws += align256(r2 * 3 * 4);
     float* st = reinterpret_cast<float*>(ws);
     const int64_t blocks = (rows + 255) / 256;
     if (blocks > INT_MAX) return fail(SEIS_EINVAL, "too many rows");
-    for (int k = 0; k < nstart; ++k) {
-        cudaError_t e = cudaMemcpyAsync(th, ABC_starts + (size_t)k * r * 3, r * 3 * sizeof(float),
-                                        cudaMemcpyDeviceToDevice, s);
+    for (int k = 0; k < nstart; k += 2) {
+        const int npair = (k + 1 < nstart) ? 2 : 1;      // an odd last start runs alone
+        cudaError_t e = cudaMemcpyAsync(th, ABC_starts + (size_t)k * r * 3,
+                                        npair * r * 3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "crs_refine_multi start copy");
-        rc = refine_run(p, th, lo3, hi3, steps, step0, w, S, g, st, ws_refine, rows, s);
+        rc = npair == 2 ? refine_run_pair(p, th, lo3, hi3, steps, step0, w, S, g, st, ws_refine,
+                                          rows, s)
+                        : refine_run(p, th, lo3, hi3, steps, step0, w, S, g, st, ws_refine, rows,
+                                     s);
         if (rc) return rc;
-        keep_best_kernel<<<(unsigned)blocks, 256, 0, s>>>(rows, k, th, S, g, st, ABC_out, S_out,
-                                                          grad_out, stack_out);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "crs_refine_multi keep");
+        for (int q = 0; q < npair; ++q) {                 // start k before start k+1 (ties)
+            keep_best_kernel<<<(unsigned)blocks, 256, 0, s>>>(
+                rows, k + q, th + q * r * 3, S + q * r, g + q * r * 3, st + q * r, ABC_out,
+                S_out, grad_out, stack_out);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "crs_refine_multi keep");
+        }
     }
     return SEIS_OK;
 }

@@ -283,6 +283,29 @@ def test_refine_multi(seis, line, coarse_starts):
     assert close.mean() >= 0.9
 
 
+@pytest.mark.parametrize("nstart", [2, 3])
+def test_refine_multi_pairs_equal_single_refinements_bitwise(seis, line, coarse_starts, nstart):
+    """crs_refine_multi refines the starts two at a time in one paired evaluation kernel (an
+    odd last start alone); its result equals the best of separate crs_refine runs, chosen
+    with the earlier start on ties, bit for bit."""
+    ds, g, ap = line
+    lo, hi = _ranges()
+    _, starts = coarse_starts
+    st = torch.from_numpy(starts[:nstart].astype(np.float32)).cuda()
+    multi = seis.crs_refine_multi(g, ap, st, lo, hi, steps=6, step0=0.05, w=11)
+    single = [seis.crs_refine(g, ap, st[k], lo, hi, steps=6, step0=0.05, w=11)
+              for k in range(nstart)]
+    torch.cuda.synchronize()
+    seis.device_status()
+    best = {k: v.clone() for k, v in single[0].items()}
+    for r in single[1:]:
+        better = r["S"] > best["S"]
+        for k in best:
+            best[k][better] = r[k][better]
+    for k in ("theta", "S", "grad", "stack"):
+        assert torch.equal(multi[k], best[k]), k
+
+
 def test_refine_workload_sample(seis):
     """The refinement workload (aperture +-8 CMPs = 816 traces, 2000 samples) on two central
     CMPs: both sides refine from the oracle's 4 best 7 x 7 x 11 candidates of every row; the
