@@ -54,15 +54,37 @@ __device__ __forceinline__ void decode_item(const BatchParams& P, const ItemView
     cc = P.poolC[v.c_off + ic];
 }
 
-// Largest item i in [lo, hi) with task_off[i] <= t.
-__device__ __forceinline__ int64_t item_of_task(const int64_t* task_off, int64_t lo, int64_t hi,
-                                                int64_t t) {
+// Largest item i in [lo, hi) with task_off[i] <= t (task_off non-decreasing), found by the
+// whole warp: each round the 32 lanes probe 32 evenly spaced entries of the interval at
+// once, so a table of N items takes about log32(N) rounds of loads instead of log2(N)
+// dependent ones.  Every lane returns the same item.
+__device__ __forceinline__ int64_t item_of_task_warp(const int64_t* task_off, int64_t lo,
+                                                     int64_t hi, int64_t t) {
+    const int lane = threadIdx.x & 31;
     while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) / 2;
-        if (task_off[mid] <= t) lo = mid; else hi = mid;
+        const int64_t span = hi - lo;
+        const int64_t step = (span + 31) / 32;            // probes lo + lane * step
+        const int64_t probe = lo + (int64_t)lane * step;
+        const bool le = probe < hi && task_off[probe] <= t;
+        const unsigned m = __ballot_sync(kFull, le);     // a prefix of the lanes (lane 0 set)
+        const int k = 31 - __clz(m);                     // last probe with task_off <= t
+        const int64_t nlo = lo + (int64_t)k * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
     }
     return lo;
 }
+
+// The search kernel's shared memory plus, per ring slot, the candidates of the pass that
+// the slot's stage starts and the task's sizes: the producer has them in registers when it
+// bounds the pass, so consumers take them from here instead of loading the item table and
+// the candidate pools from global memory at every pass (for small-fold items a pass is a
+// single stage of a few traces, and that latency would stall every warp once per stage).
+struct BatchSmem {
+    SearchSmem s;
+    float4 cand[kSlots][32];     // (A, B, C, -) of candidates pass * kCB + lane
+    int2 sizes[kSlots];          // (ncand, rows) of the stage's item
+};
 
 template <int W, class CFG>
 __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchParams P) {
@@ -72,7 +94,8 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
     constexpr int kCB = CFG::kCB;
     constexpr int kConsumers = CFG::kConsumers;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SearchSmem& sm = *reinterpret_cast<SearchSmem*>(smem_raw);
+    BatchSmem& bsm = *reinterpret_cast<BatchSmem*>(smem_raw);
+    SearchSmem& sm = bsm.s;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t t_begin = P.task_off[P.item_begin];
@@ -94,6 +117,10 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
         bool have = false;
         ItemView it{};
         int64_t item = 0;
+        // the next task is claimed one task ahead, so the atomic's latency passes while the
+        // current task's stages are produced
+        unsigned long long next = 0;
+        if (lane == 0) next = atomicAdd(P.counter, 1ull);
         int tile = 0, n0 = 0, n_last = 0, npass = 0;
         int pl_pass = 0, pl_t = 0, pl_bpass = -1;
         float bA0 = 0.f, bA1 = 0.f, bB0 = 0.f, bB1 = 0.f, bC0 = 0.f, bC1 = 0.f;
@@ -109,14 +136,13 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
             __syncwarp();
             bool finished = sm.abort_flag != 0;
             if (!finished && (!have || pl_pass >= npass)) {
-                unsigned long long t = 0;
-                if (lane == 0) t = atomicAdd(P.counter, 1ull);
-                t = __shfl_sync(kFull, t, 0);
+                const unsigned long long t = __shfl_sync(kFull, next, 0);
                 const int64_t tk = t_begin + (int64_t)t;
                 if (tk >= t_end) {
                     finished = true;
                 } else {
-                    item = item_of_task(P.task_off, P.item_begin, P.item_end, tk);
+                    if (lane == 0) next = atomicAdd(P.counter, 1ull);
+                    item = item_of_task_warp(P.task_off, P.item_begin, P.item_end, tk);
                     tile = (int)(tk - P.task_off[item]);
                     it = load_item(P, item);
                     n0 = tile * 32;
@@ -134,6 +160,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
                 mbar_arrive(&sm.full[slot]);
                 break;
             }
+            const int first = (pl_t == 0);
             if (pl_bpass != pl_pass) {   // candidate bounds of this pass (one per lane)
                 const int c = pl_pass * kCB + lane;
                 float a = 0.f, b = 0.f, cc = 0.f;
@@ -143,8 +170,10 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
                 bB0 = warp_min(v ? b : FLT_MAX);  bB1 = warp_max(v ? b : -FLT_MAX);
                 bC0 = warp_min(v ? cc : FLT_MAX); bC1 = warp_max(v ? cc : -FLT_MAX);
                 pl_bpass = pl_pass;
+                // the pass's first stage carries its candidates (released with the stage)
+                bsm.cand[slot][lane] = make_float4(a, b, cc, 0.f);
+                if (lane == 0) bsm.sizes[slot] = make_int2(it.ncand, it.nrows);
             }
-            const int first = (pl_t == 0);
             int nfit = 0;
             unsigned allv = 0u;
             const int ntr = produce_stage<true, HW>(
@@ -173,13 +202,13 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
     Accum<W, CFG> acc;
     #pragma unroll
     for (int r = 0; r < kR; ++r) acc.cidx[r] = INT_MAX;
-    ItemView it{};
+    int64_t task_item = 0;                       // the item of the current task
+    int ncand = 0;
     RowConst rc = row_const(false, 0);
     bool act = false;
     int nrow = 0;
     float bestS = -1.f, bestT = 0.f;
     int bestC = INT_MAX;
-    auto decode = [&](int c, float& a, float& b, float& cc) { decode_item(P, it, c, a, b, cc); };
 
     for (int s = 0;; ++s) {
         const int slot = s % kSlots;
@@ -190,19 +219,31 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
         }
         const StageDesc d = sm.desc[slot];
         if (d.end) break;
-        if (d.first && d.pass == 0) {            // a new task
-            it = load_item(P, d.item);
-            nrow = d.tile * 32 + lane;
-            act = nrow < it.nrows;
-            rc = row_const(act, nrow);
+        if (d.first) {
+            const int2 sz = bsm.sizes[slot];
+            ncand = sz.x;
+            if (d.pass == 0) {                   // a new task
+                task_item = d.item;
+                nrow = d.tile * 32 + lane;
+                act = nrow < sz.y;
+                rc = row_const(act, nrow);
+            }
+            const int cbase = d.pass * kCB;
+            const float4* cand = bsm.cand[slot];
+            accum_begin(acc, cbase + warp * kR, ncand, [&](int c, float& a, float& b, float& cc) {
+                const float4 v = cand[c - cbase];
+                a = v.x;
+                b = v.y;
+                cc = v.z;
+            });
         }
-        if (d.first) accum_begin(acc, d.pass * kCB + warp * kR, it.ncand, decode);
         const int ntr = min(d.ntr, kChunkT);
         const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
-        if (ntr > 0 && acc.cidx[0] < it.ncand)
+        if (ntr > 0 && acc.cidx[0] < ncand)
             accum_stage<true, W, CFG>(acc, sm.meta[slot], ntr, d.allv, slot_base, rc, zidx, smf);
-        if (d.last) accum_end(acc, it.ncand, nullptr, bestS, bestC, bestT);
+        if (d.last) accum_end(acc, ncand, nullptr, bestS, bestC, bestT);
         if (d.task_end) {                        // the task's last stage: argmax and outputs
+            const ItemView it = load_item(P, task_item);
             sm.redS[warp][lane] = bestS;
             sm.redC[warp][lane] = bestC;
             sm.redT[warp][lane] = bestT;
@@ -235,7 +276,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
 template <int W, class CFG>
 cudaError_t launch_batch_w(const BatchParams& p, int grid, cudaStream_t stream) {
     static bool configured[64] = {};
-    const int smem = (int)sizeof(SearchSmem);
+    const int smem = (int)sizeof(BatchSmem);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;

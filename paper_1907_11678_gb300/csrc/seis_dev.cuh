@@ -67,12 +67,15 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
 }
 
 // Wait for the phase with the given parity; gives up after limit_ns and returns false.
+// The waiting thread is suspended in hardware between tests; the timer is read only every
+// 32 tests, so a long wait takes few issue slots from the warps doing the work.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
-        if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
         if (global_ns() - t0 > limit_ns) return false;
     }
 }
@@ -88,20 +91,12 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait of a warp that is usually early (a producer that runs ahead of its consumers by
-// several ring slots): sleep between tests with an exponential back-off up to ~1 us, so
-// that the waiting warp takes almost no issue slots from the warps doing the work.  Gives
-// up after limit_ns and returns false.
+// several ring slots).  __nanosleep may return long before the requested time, so a
+// sleep-and-test loop keeps issuing; the suspending try_wait of mbar_wait_bounded does not.
+// Gives up after limit_ns and returns false.
 __device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity,
                                                   unsigned long long limit_ns = kWaitLimitNs) {
-    if (mbar_test_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    unsigned ns = 64;
-    for (;;) {
-        __nanosleep(ns);
-        if (mbar_test_wait(bar, parity)) return true;
-        if (ns < 1024) ns <<= 1;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
+    return mbar_wait_bounded(bar, parity, limit_ns);
 }
 
 // 1-D bulk copy global -> shared through the TMA engine; completion is counted in bytes
