@@ -12,8 +12,10 @@ the same shape bucket.
 
 Other workloads (--workload): crs-line (1024 central CMPs, aperture +-10 CMPs, fold 48,
 21x21x41 grid; --centrals limits the centrals), batch (10,000 uneven CMP/CRS items in one
-persistent launch; --items), refine (512 central CMPs, coarse 7x7x11 search + 20
-gradient-ascent steps, against the dense 41x41x81 search on --dense-centrals centrals).
+persistent launch; --items), refine (512 central CMPs, coarse 7x7x11 search, its 128 best
+candidates per row each refined by 20 gradient-ascent steps, against the dense 41x41x81
+search on --dense-centrals centrals).  The default cmp-line run also times 64 centrals of
+crs-line and the refine workload and reports them as its "crs" and "refine" sub-objects.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
 same workload (the reference arm of this build: the paper publishes no code).  Under
@@ -555,8 +557,10 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
     ap = seis.crs_aperture(g, central, ds["apm"])
     (alo, ahi), (blo, bhi), (clo, chi) = synth.crs_ranges()
     lo, hi = [alo, blo, clo], [ahi, bhi, chi]
-    A7, B7, C11 = _crs_grids(seis, dev, synth, 7, 7, 11)
-    nstart, steps = args.starts, 20
+    ncA, ncB, ncC = (int(v) for v in args.coarse.split(","))
+    A7, B7, C11 = _crs_grids(seis, dev, synth, ncA, ncB, ncC)
+    nstart, steps = args.starts, args.refine_steps
+    local_max = args.start_rule == "localmax"
     ws = torch.empty(seis.load_library().seis_refine_multi_workspace_size(ap.rows) + 256,
                      dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -565,7 +569,7 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
     def refine_all(record=False):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)] if record else None
         coarse = seis.crs_semblance(g, ap, A7, B7, C11, w=W, want_cube=True)
-        starts = seis.crs_top_starts(coarse["S"], A7, B7, C11, nstart)
+        starts = seis.crs_top_starts(coarse["S"], A7, B7, C11, nstart, local_max=local_max)
         if record:
             ev[0].record(stream)
         ref = seis.crs_refine_multi(g, ap, starts, lo, hi, steps=steps, step0=0.05, w=W,
@@ -588,6 +592,12 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
     search_ms = float(np.mean(kern)) - multi_ms       # coarse search + start selection
     coarse, ref = refine_all()
     one = seis.crs_refine(g, ap, coarse["best_ABC"], lo, hi, steps=steps, step0=0.05, w=W)
+    # the other start rule, untimed, for comparison (optional: it repeats the refinement)
+    other = None
+    if args.compare_start_rules:
+        other = seis.crs_refine_multi(g, ap, seis.crs_top_starts(coarse["S"], A7, B7, C11, nstart,
+                                                                 local_max=not local_max),
+                                      lo, hi, steps=steps, step0=0.05, w=W, workspace=ws)
     # the dense 41x41x81 search on a slice of centrals, timed and extrapolated
     nd = min(args.dense_centrals, len(central))
     apd = seis.crs_aperture(g, central[:nd], ds["apm"])
@@ -617,7 +627,7 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
                 "rows_above_dense": float(np.mean(gap < 0)),
                 "median_S_refined_minus_dense": float(np.median(-gap)), "by_S_dense": per}
     trace_rows = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 2000
-    inter_coarse = trace_rows * 539
+    inter_coarse = trace_rows * ncA * ncB * ncC
     inter_eval = trace_rows * nstart * (steps + 1)
     inter_refine = inter_coarse + inter_eval
     launches = 2 + nstart * (2 * steps + 3)
@@ -630,10 +640,12 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
                         args, world,
                         {"workload": f"refine: {len(central)} central CMPs of 512, aperture +-8 "
                                      "CMPs (816 traces), "
-                                     f"2000 samples @4ms; coarse 7x7x11, its {nstart} best "
-                                     f"candidates per row each refined by {steps} projected "
-                                     "BFGS gradient-ascent steps, best kept; vs dense 41x41x81",
-                         "starts": nstart, "steps": steps, "dense_centrals_timed": nd,
+                                     f"2000 samples @4ms; coarse {ncA}x{ncB}x{ncC}, {nstart} "
+                                     f"starts per row ({'the best local maxima of the coarse cube' if local_max else 'the best coarse candidates'}) "
+                                     f"each refined by {steps} projected BFGS gradient-ascent "
+                                     "steps, best kept; vs dense 41x41x81",
+                         "starts": nstart, "start_rule": args.start_rule, "steps": steps,
+                         "dense_centrals_timed": nd,
                          "dense_ctas": int(nd * ((2000 + 31) // 32)),
                          "resident_cta_slots": 2 * sms},
                         {"refine_ms": refine_ms, "coarse_search_ms": search_ms,
@@ -642,6 +654,8 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
                          "speedup_refine_vs_dense": dense_ms / refine_ms,
                          **quality(ref["S"]),
                          "one_start (untimed, for comparison)": quality(one["S"]),
+                         **({f"start rule {'top' if local_max else 'localmax'} (untimed, for comparison)":
+                             quality(other["S"])} if other is not None else {}),
                          "mean_S_gain_over_coarse": float((ref["S"] - coarse["best_S"]).mean()),
                          "roofline": {"bound": "alu", "kernel": "eval_kernel<CRS, w=11, adjoint>",
                                       "achieved": ach_eval, "peak": peak, "unit": "TFLOP/s",
@@ -961,7 +975,14 @@ def main():
     ap.add_argument("--items", type=int, default=10000, help="batch: items")
     ap.add_argument("--dense-centrals", type=int, default=24,
                     help="refine: dense-grid slice (24 x 63 tiles = 4.97 waves of 304 CTAs)")
-    ap.add_argument("--starts", type=int, default=16, help="refine: coarse starts per row")
+    ap.add_argument("--starts", type=int, default=128, help="refine: coarse starts per row")
+    ap.add_argument("--compare-start-rules", action="store_true",
+                    help="refine: also report the other start rule's quality (untimed)")
+    ap.add_argument("--coarse", default="7,7,11", help="refine: coarse grid nA,nB,nC")
+    ap.add_argument("--refine-steps", type=int, default=20, help="refine: BFGS trials per start")
+    ap.add_argument("--start-rule", default="top", choices=["localmax", "top"],
+                    help="refine: starts at the coarse cube's best local maxima or its best "
+                         "candidates")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
     ap.add_argument("--no-secondary", action="store_true",
                     help="cmp-line: leave out the crs and refine sub-objects")

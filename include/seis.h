@@ -273,6 +273,19 @@ int crs_top_starts(const float* S_cube, int64_t rows, const float* A, int32_t nA
                    const float* B, int32_t nB, const float* C, int32_t nC, int32_t nstart,
                    float* ABC_starts, void* stream);
 
+/* Starting points at the local maxima of the coarse cube (no counterpart in the paper): as
+ * crs_top_starts, but a row's starts are first its local maxima -- candidates whose
+ * (S, -index) exceeds that of every neighbour in the grid (ia, ib, ic each within +-1, up to
+ * 26 neighbours) -- in the order S descending, index ascending, and only then, if the row
+ * has fewer than nstart local maxima, its best other candidates in that order.  Starts at
+ * distinct local maxima climb distinct hills of S, where the nstart best candidates often
+ * crowd around one.  nA*nB*nC <= SEIS_LOCAL_MAX_CANDIDATES (SEIS_EUNSUPPORTED beyond).
+ * Arguments, layout and errors otherwise as crs_top_starts (one launch). */
+#define SEIS_LOCAL_MAX_CANDIDATES 32768
+int crs_local_max_starts(const float* S_cube, int64_t rows, const float* A, int32_t nA,
+                         const float* B, int32_t nB, const float* C, int32_t nC,
+                         int32_t nstart, float* ABC_starts, void* stream);
+
 /* Multi-start refinement (no counterpart in the paper): crs_refine from each of the nstart
  * starting operators ABC_starts [nstart][rows][3] (device, read only), keeping per row the
  * result with the highest S (the earlier start on ties) in ABC_out [rows][3], S_out,

@@ -316,6 +316,44 @@ def top_starts(S_cube, A, B, C, nstart):
     return out
 
 
+def local_max_flags(S_cube, nA, nB, nC):
+    """Local maxima of each row's cube over the grid [nA, nB, nC]: entry c is one when its
+    (S, -c) exceeds that of every neighbour (ia, ib, ic each within +-1, inside the grid).
+    Plain definition, vectorised over rows: returns bool [rows, nA*nB*nC]."""
+    S = np.asarray(S_cube, np.float64).reshape(-1, nA, nB, nC)
+    idx = np.arange(nA * nB * nC).reshape(nA, nB, nC)
+    is_max = np.ones(S.shape, bool)
+    for da in (-1, 0, 1):
+        for db in (-1, 0, 1):
+            for dc in (-1, 0, 1):
+                if da == db == dc == 0:
+                    continue
+                # target slice [a0:a1] sees neighbours at [a0+da : a1+da]
+                sa = slice(max(0, -da), nA - max(0, da)); na = slice(max(0, da), nA + min(0, da))
+                sb = slice(max(0, -db), nB - max(0, db)); nbs = slice(max(0, db), nB + min(0, db))
+                sc = slice(max(0, -dc), nC - max(0, dc)); ncs = slice(max(0, dc), nC + min(0, dc))
+                v, u = S[:, sa, sb, sc], S[:, na, nbs, ncs]
+                iv, iu = idx[sa, sb, sc], idx[na, nbs, ncs]
+                beaten = (u > v) | ((u == v) & (iu < iv))
+                is_max[:, sa, sb, sc] &= ~beaten
+    return is_max.reshape(S.shape[0], -1)
+
+
+def local_max_starts(S_cube, A, B, C, nstart):
+    """Starts at the cube's local maxima: per row, the local maxima (local_max_flags) in the
+    order S descending, candidate index ascending, then the other candidates in that order;
+    the first nstart, decoded to operators [nstart, rows, 3] (cand = (ia*nB + ib)*nC + ic)."""
+    S_cube = np.asarray(S_cube, np.float64)
+    A, B, C = (np.asarray(v) for v in (A, B, C))
+    nA, nB, nC = len(A), len(B), len(C)
+    flags = local_max_flags(S_cube, nA, nB, nC)
+    idx = np.broadcast_to(np.arange(S_cube.shape[1]), S_cube.shape)
+    order = np.lexsort((idx, -S_cube, ~flags), axis=-1)[:, :nstart]      # last key first
+    ia, rem = np.divmod(order, nB * nC)
+    ib, ic = np.divmod(rem, nC)
+    return np.stack([A[ia], B[ib], C[ic]], axis=-1).transpose(1, 0, 2).astype(np.float64)
+
+
 def crs_refine_multi(ds, nb, starts, lo3, hi3, steps=20, step0=0.05, w=11, rows=None,
                      nthreads=0) -> Result:
     """crs_refine from each start [nstart, rows, 3]; per row the result with the highest

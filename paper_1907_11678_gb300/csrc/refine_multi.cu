@@ -58,6 +58,91 @@ __global__ void top_starts_kernel(const float* __restrict__ S, int64_t rows, int
     (void)nA;
 }
 
+// Starts at the local maxima of a row's coarse cube: one warp per row.  The warp first
+// marks, in a bitmask in shared memory, every candidate whose (S, -index) exceeds that of
+// each of its grid neighbours (ia, ib, ic each within +-1); then k selection passes take
+// the best entries in the order (local maxima first, then S descending, then index
+// ascending), as top_starts_kernel does without the first key.
+constexpr int kLmWarps = 4;                      // rows (warps) per block
+__global__ void local_max_starts_kernel(const float* __restrict__ S, int64_t rows, int nA,
+                                        int nB, int nC, const float* __restrict__ A,
+                                        const float* __restrict__ B,
+                                        const float* __restrict__ C, int k,
+                                        float* __restrict__ out) {
+    extern __shared__ unsigned lm_bits[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * kLmWarps + warp;
+    if (row >= rows) return;                       // uniform over the warp
+    const int ncand = nA * nB * nC;
+    const int nwords = (ncand + 31) / 32;
+    unsigned* bits = lm_bits + warp * nwords;
+    const float* Sr = S + row * (int64_t)ncand;
+    for (int w0 = 0; w0 < nwords; ++w0) {          // 32 candidates per round, one per lane
+        const int c = w0 * 32 + lane;
+        bool lmax = false;
+        if (c < ncand) {
+            const int ia = c / (nB * nC), rem = c - ia * nB * nC;
+            const int ib = rem / nC, ic = rem - ib * nC;
+            const float v = Sr[c];
+            lmax = true;
+            for (int da = -1; da <= 1 && lmax; ++da) {
+                const int a = ia + da;
+                if (a < 0 || a >= nA) continue;
+                for (int db = -1; db <= 1 && lmax; ++db) {
+                    const int b = ib + db;
+                    if (b < 0 || b >= nB) continue;
+                    for (int dc = -1; dc <= 1; ++dc) {
+                        const int cc = ic + dc;
+                        if (cc < 0 || cc >= nC || (da == 0 && db == 0 && dc == 0)) continue;
+                        const int n = (a * nB + b) * nC + cc;
+                        const float u = Sr[n];
+                        if (u > v || (u == v && n < c)) { lmax = false; break; }
+                    }
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, lmax);
+        if (lane == 0) bits[w0] = m;
+    }
+    __syncwarp();
+    // selection: key (group, S, index) with group 0 for local maxima, ordered (group asc,
+    // S desc, index asc); pass j takes the smallest key after pass j-1's pick
+    int lastG = -1, lastI = -1;
+    float lastS = FLT_MAX;
+    for (int j = 0; j < k; ++j) {
+        int bg = 2, bi = INT_MAX;
+        float bs = -FLT_MAX;
+        for (int c = lane; c < ncand; c += 32) {
+            const int g = ((bits[c >> 5] >> (c & 31)) & 1u) ? 0 : 1;
+            const float v = Sr[c];
+            const bool after = g > lastG || (g == lastG && (v < lastS || (v == lastS && c > lastI)));
+            const bool better = g < bg || (g == bg && (v > bs || (v == bs && c < bi)));
+            if (after && better) { bg = g; bs = v; bi = c; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const int og = __shfl_xor_sync(0xffffffffu, bg, o);
+            const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (og < bg || (og == bg && (os > bs || (os == bs && oi < bi)))) {
+                bg = og; bs = os; bi = oi;
+            }
+        }
+        if (bi == INT_MAX) bi = 0;                   // unreachable for k <= ncand
+        lastG = bg;
+        lastS = bs;
+        lastI = bi;
+        if (lane == 0) {
+            const int ia = bi / (nB * nC), rem = bi - ia * nB * nC;
+            const int ib = rem / nC, ic = rem - ib * nC;
+            float* o = out + ((int64_t)j * rows + row) * 3;
+            o[0] = A[ia];
+            o[1] = B[ib];
+            o[2] = C[ic];
+        }
+    }
+}
+
 // Keep, per row, the refinement with the highest S (the earlier start on ties).
 __global__ void keep_best_kernel(int64_t rows, int start, const float* __restrict__ th,
                                  const float* __restrict__ S, const float* __restrict__ g,
@@ -103,6 +188,30 @@ extern "C" int crs_top_starts(const float* S_cube, int64_t rows, const float* A,
 
 // Starts are refined two at a time (the paired evaluation kernel), so the refinement state
 // and the per-start results hold two starts of every row.
+extern "C" int crs_local_max_starts(const float* S_cube, int64_t rows, const float* A,
+                                    int32_t nA, const float* B, int32_t nB, const float* C,
+                                    int32_t nC, int32_t nstart, float* ABC_starts, void* stream) {
+    if (!S_cube || !A || !B || !C || !ABC_starts) return fail(SEIS_EINVAL, "an array is NULL");
+    if (rows < 1) return fail(SEIS_EINVAL, "rows must be >= 1");
+    if (nA < 1 || nB < 1 || nC < 1) return fail(SEIS_EINVAL, "empty candidate axis");
+    const int64_t ncand = (int64_t)nA * nB * nC;
+    if (ncand > SEIS_LOCAL_MAX_CANDIDATES)
+        return fail(SEIS_EUNSUPPORTED, "%lld candidates, at most %d", (long long)ncand,
+                    SEIS_LOCAL_MAX_CANDIDATES);
+    if (nstart < 1 || nstart > ncand)
+        return fail(SEIS_EINVAL, "nstart = %d outside [1, %lld]", nstart, (long long)ncand);
+    const int64_t blocks = (rows + kLmWarps - 1) / kLmWarps;
+    if (blocks > INT_MAX) return fail(SEIS_EINVAL, "too many rows");
+    // one bit per candidate and row: at most 16 KB per block, within the default limit
+    const size_t smem = (size_t)kLmWarps * ((ncand + 31) / 32) * sizeof(unsigned);
+    local_max_starts_kernel<<<(unsigned)blocks, 32 * kLmWarps, smem,
+                              static_cast<cudaStream_t>(stream)>>>(
+        S_cube, rows, nA, nB, nC, A, B, C, nstart, ABC_starts);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "crs_local_max_starts launch");
+    return SEIS_OK;
+}
+
 extern "C" size_t seis_refine_multi_workspace_size(int64_t rows) {
     if (rows < 0) return 0;
     const size_t r2 = 2 * (size_t)rows;

@@ -84,6 +84,7 @@ def load_library(path: str | None = None):
             lib.crs_refine.argtypes = [vp, vp, vp, vp, vp, i32, f32, i32, vp, vp, vp, vp,
                                        ctypes.c_size_t, i64, vp]
             lib.crs_top_starts.argtypes = [vp, i64, vp, i32, vp, i32, vp, i32, i32, vp, vp]
+            lib.crs_local_max_starts.argtypes = lib.crs_top_starts.argtypes
             lib.seis_refine_multi_workspace_size.argtypes = [i64]
             lib.seis_refine_multi_workspace_size.restype = ctypes.c_size_t
             lib.crs_refine_multi.argtypes = [vp, vp, vp, i32, vp, vp, i32, f32, i32, vp, vp, vp,
@@ -112,6 +113,7 @@ def load_library(path: str | None = None):
                          "seis_autotune_cmp", "seis_autotune_crs", "seis_autotune_save",
                          "seis_autotune_load", "seis_autotune_clear", "stack",
                          "crs_semblance_grad", "crs_refine", "crs_top_starts",
+                         "crs_local_max_starts",
                          "crs_refine_multi", "seis_batch_semblance", "seis_autotune_batch",
                          "seis_crs_aperture_offset", "crs_pragmatic", "cmp_semblance_t0win",
                          "crs_semblance_t0win", "seis_velocity_grid", "seis_linear_grid",
@@ -525,9 +527,10 @@ def crs_refine(g: Gathers, ap: "Aperture", ABC0: torch.Tensor, lo3, hi3, steps: 
 
 
 def crs_top_starts(S_cube: torch.Tensor, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor,
-                   nstart: int, stream=None) -> torch.Tensor:
+                   nstart: int, stream=None, local_max: bool = False) -> torch.Tensor:
     """The nstart best coarse candidates of every row of a CRS cube [rows, nA*nB*nC] as
-    operators [nstart, rows, 3] (include/seis.h: crs_top_starts)."""
+    operators [nstart, rows, 3] (include/seis.h: crs_top_starts; with local_max, the best
+    local maxima of the cube first: crs_local_max_starts)."""
     lib = load_library()
     dev = S_cube.device
     A, B, C = _input(A, "A", dev), _input(B, "B", dev), _input(C, "C", dev)
@@ -537,8 +540,9 @@ def crs_top_starts(S_cube: torch.Tensor, A: torch.Tensor, B: torch.Tensor, C: to
     S_cube = _input(S_cube, "S_cube", dev)
     rows = S_cube.shape[0]
     out = torch.empty((nstart, rows, 3), dtype=torch.float32, device=dev)
-    _check(lib.crs_top_starts(_ptr(S_cube), rows, _ptr(A), A.numel(), _ptr(B), B.numel(),
-                              _ptr(C), C.numel(), int(nstart), _ptr(out), _stream_handle(stream)))
+    fn = lib.crs_local_max_starts if local_max else lib.crs_top_starts
+    _check(fn(_ptr(S_cube), rows, _ptr(A), A.numel(), _ptr(B), B.numel(), _ptr(C), C.numel(),
+              int(nstart), _ptr(out), _stream_handle(stream)))
     return out
 
 

@@ -260,6 +260,22 @@ def test_top_starts_exact(seis):
         seis.crs_top_starts(t(cube), t(A), t(B), t(C), nA * nB * nC + 1)
 
 
+def test_local_max_starts_exact(seis):
+    """Starts at the cube's local maxima: integer work on cubes full of ties, bit-exact
+    against the oracle's definition, for several grid shapes (one axis of length 1 too)."""
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    for rows, (nA, nB, nC), k in [(333, (5, 3, 7), 6), (100, (7, 7, 11), 16), (64, (1, 1, 41), 5),
+                                  (50, (4, 1, 3), 12)]:
+        cube = synth.score_cube(rows, nA * nB * nC, levels=4, seed=nA + nC)
+        A = np.float32(np.linspace(-1, 1, nA)); B = np.float32(np.linspace(2, 3, nB))
+        C = np.float32(np.linspace(5, 9, nC))
+        got = seis.crs_top_starts(t(cube), t(A), t(B), t(C), k, local_max=True).cpu().numpy()
+        want = oracle.local_max_starts(cube, A, B, C, k).astype(np.float32)
+        np.testing.assert_array_equal(got, want)
+    with pytest.raises(seis.SeisError):
+        seis.crs_top_starts(t(cube), t(A), t(B), t(C), nA * nB * nC + 1, local_max=True)
+
+
 def test_refine_multi(seis, line, coarse_starts):
     ds, g, ap = line
     lo, hi = _ranges()

@@ -161,3 +161,54 @@ def test_refine_trajectory_records_every_trial():
         if acc.any():
             assert r.S[i] == r.traj[i, made, 3][acc][-1]
             assert np.all(np.diff(r.traj[i, made, 3][acc]) >= 0)
+
+
+# --- starts at the coarse cube's local maxima -------------------------------------------
+
+def _brute_local_max(S, nA, nB, nC):
+    """Plain loops over every entry and its grid neighbours."""
+    out = np.zeros(S.shape, bool)
+    for r in range(S.shape[0]):
+        for c in range(S.shape[1]):
+            ia, rem = divmod(c, nB * nC)
+            ib, ic = divmod(rem, nC)
+            ok = True
+            for da in (-1, 0, 1):
+                for db in (-1, 0, 1):
+                    for dc in (-1, 0, 1):
+                        a, b, cc = ia + da, ib + db, ic + dc
+                        if (da, db, dc) == (0, 0, 0) or not (0 <= a < nA and 0 <= b < nB
+                                                             and 0 <= cc < nC):
+                            continue
+                        n = (a * nB + b) * nC + cc
+                        if S[r, n] > S[r, c] or (S[r, n] == S[r, c] and n < c):
+                            ok = False
+            out[r, c] = ok
+    return out
+
+
+def test_local_max_flags_bruteforce():
+    rng = np.random.default_rng(21)
+    for nA, nB, nC in [(3, 2, 4), (1, 1, 7), (4, 3, 1), (2, 5, 3), (3, 3, 3)]:
+        S = rng.integers(0, 4, size=(6, nA * nB * nC)) / 4.0         # many ties
+        np.testing.assert_array_equal(oracle.local_max_flags(S, nA, nB, nC),
+                                      _brute_local_max(S, nA, nB, nC))
+
+
+def test_local_max_starts_hand_worked():
+    """Grid 1 x 1 x 5, S = 0.1 0.5 0.2 0.7 0.3: local maxima 3 (0.7) and 1 (0.5) come first,
+    then the others by S; with S = 0.5 0.5 0.1 the tie goes to the lower index, so only
+    entry 0 is a local maximum.  A 2 x 2 x 2 cube has one local maximum at its largest
+    entry."""
+    A, B, C = [0.0], [0.0], [10.0, 11.0, 12.0, 13.0, 14.0]
+    got = oracle.local_max_starts(np.array([[0.1, 0.5, 0.2, 0.7, 0.3]]), A, B, C, 5)
+    np.testing.assert_array_equal(got[:, 0, 2], [13.0, 11.0, 14.0, 12.0, 10.0])
+    got = oracle.local_max_starts(np.array([[0.5, 0.5, 0.1]]), A, B, C[:3], 3)
+    np.testing.assert_array_equal(got[:, 0, 2], [10.0, 11.0, 12.0])
+    flags = oracle.local_max_flags(np.array([[0.5, 0.5, 0.1]]), 1, 1, 3)
+    np.testing.assert_array_equal(flags, [[True, False, False]])
+    cube = np.array([[0.1, 0.2, 0.3, 0.9, 0.4, 0.5, 0.6, 0.7]])      # 2 x 2 x 2
+    flags = oracle.local_max_flags(cube, 2, 2, 2)
+    np.testing.assert_array_equal(flags[0], np.arange(8) == 3)
+    got = oracle.local_max_starts(cube, [1.0, 2.0], [3.0, 4.0], [5.0, 6.0], 2)
+    np.testing.assert_array_equal(got[:, 0], [[1.0, 4.0, 6.0], [2.0, 4.0, 6.0]])
