@@ -102,6 +102,16 @@ int seis_device_status(void* stream);
  * next seis_device_status() reports it and the context stays usable. */
 int seis_selftest_wait_timeout(int32_t limit_us, void* stream);
 
+/* Self-test of the fast arithmetic of the traveltime (no counterpart in the paper, which
+ * takes the square root of Eq. 2's traveltime exactly): the search, t0-window and
+ * evaluation kernels form u = sqrt(radicand) and 1/(u + p) with the hardware's approximate
+ * square root and reciprocal (PTX sqrt.approx.ftz.f32, rcp.approx.ftz.f32).  This runs both
+ * on every float in [1, 4) (all mantissas under both exponent parities; the relative error
+ * repeats with the exponent) and writes, to max_rel_err[0] and [1] (device, 2 floats,
+ * caller-owned), the largest relative error of each against an FP64 reference.
+ * Asynchronous, one launch.  Errors: SEIS_EINVAL, SEIS_ECUDA. */
+int seis_selftest_fast_math(float* max_rel_err, void* stream);
+
 /* Search kernel variants.  The semblance search kernels come in several tile shapes and
  * arithmetic forms (consumer warps per CTA, candidates per thread, scalar / packed f32x2 /
  * hybrid FP32 accumulation); every variant computes bit-identical results.  A launch uses

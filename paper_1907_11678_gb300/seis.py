@@ -101,6 +101,7 @@ def load_library(path: str | None = None):
                                                  vp, vp, vp, vp, i64, vp, ctypes.c_size_t, vp]
             lib.seis_selftest_wait_timeout.argtypes = [i32, vp]
             lib.seis_velocity_grid.argtypes = [ctypes.c_double, ctypes.c_double, i32, vp, vp]
+            lib.seis_selftest_fast_math.argtypes = [vp, vp]
             lib.seis_linear_grid.argtypes = [ctypes.c_double, ctypes.c_double, i32, vp, vp]
             lib.seis_autotune_batch.argtypes = [vp, vp, i64, vp, i32, vp, i32, vp, i32, i32, vp,
                                                 vp, vp, vp, i64, vp, ctypes.c_size_t, i32, vp,
@@ -117,6 +118,7 @@ def load_library(path: str | None = None):
                          "crs_refine_multi", "seis_batch_semblance", "seis_autotune_batch",
                          "seis_crs_aperture_offset", "crs_pragmatic", "cmp_semblance_t0win",
                          "crs_semblance_t0win", "seis_velocity_grid", "seis_linear_grid",
+                         "seis_selftest_fast_math",
                          "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -690,6 +692,15 @@ def autotune_batch(g: Gathers, b: Batch, w: int = 11, reps: int = 1, stream=None
 def selftest_wait_timeout(limit_us: int = 10000, stream=None) -> None:
     """Launch the bounded-wait self-test (include/seis.h: seis_selftest_wait_timeout)."""
     _check(load_library().seis_selftest_wait_timeout(int(limit_us), _stream_handle(stream)))
+
+
+def selftest_fast_math(stream=None) -> tuple[float, float]:
+    """Largest relative errors of the kernels' fast square root and reciprocal over every
+    float in [1, 4) (include/seis.h: seis_selftest_fast_math)."""
+    out = torch.empty(2, dtype=torch.float32, device="cuda")
+    _check(load_library().seis_selftest_fast_math(_ptr(out), _stream_handle(stream)))
+    e = out.cpu().tolist()
+    return e[0], e[1]
 
 
 def device_status(stream=None) -> None:

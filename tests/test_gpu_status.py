@@ -32,3 +32,18 @@ def test_bounded_wait_gives_up_and_reports():
     torch.cuda.synchronize()
     seis.device_status()
     assert np.isfinite(out["best_S"].cpu().numpy()).all()
+
+
+def test_fast_traveltime_arithmetic_error_bound():
+    """The approximate square root and reciprocal of the traveltime stay within 2^-21
+    relative error (measured on every float in [1, 4)); with the cancellation-free moveout
+    D = C q / (sqrt(n^2 + C q) + n) this moves u = n + D by at most about 3 * 2^-21 * D
+    samples, below the 1e-3-sample mask-edge tolerance of the parity checks for any moveout
+    under 600 samples, and far below it for the window's interpolation fraction."""
+    from paper_1907_11678_gb300 import build, seis
+    build.build()
+    es, er = seis.selftest_fast_math()
+    torch.cuda.synchronize()
+    print(f"[fast-math] max relative error: sqrt {es:.3e} ({np.log2(es):.2f} bits), "
+          f"rcp {er:.3e} ({np.log2(er):.2f} bits)")
+    assert 0 < es <= 2.0 ** -21 and 0 < er <= 2.0 ** -21
