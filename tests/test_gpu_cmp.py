@@ -234,3 +234,44 @@ def test_linear_grids_match_oracle(seis):
         seis.velocity_grid(0.0, 4500.0, 5)
     with pytest.raises(seis.SeisError):
         seis.linear_grid(0.0, 1.0, 0)
+
+
+# --- maximum sizes ------------------------------------------------------------------------
+
+def test_cmp_max_trace_length_and_window(seis):
+    """Traces of exactly SEIS_MAX_TRACE_SAMPLES samples (12.28 s at 1 ms) with the widest
+    window (w = 15) and a velocity range whose moveouts span thousands of samples: the search
+    reports no problem and matches the oracle on sampled rows (every row of the tiles that
+    hold the record's first and last output times among them)."""
+    ns = seis.SEIS_MAX_TRACE_SAMPLES
+    ds = synth.cmp_line(3, 8, ns, 0.001, 0.0, 3000.0, 4, 2.0, seed=501)
+    assert int(np.diff(ds["trace_off"]).max()) == ns
+    C = _grid(41)
+    got = _run(seis, ds, C, w=15, cube=False)
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([rng.choice(int(ds["out_off"][-1]), 160, replace=False),
+                                     np.arange(0, 32), np.arange(ns - 32, ns + 32)]))
+    ref = oracle.cmp_semblance(ds, C, w=15, rows=rows)
+    parity.check_picks(got["best_idx"][rows], got["best_S"][rows], got["stack"][rows], ref,
+                       "cmp max trace length")
+
+
+def test_window_larger_than_a_slot_is_reported(seis):
+    """A stage window that cannot fit a shared-memory slot (a 12,280-sample trace at
+    20 km half-offset, candidates from C = 0 to 4e-6 s^2/m^2 in one pass, so one trace's
+    window spans the whole record) is dropped and reported as SEIS_EUNSUPPORTED by
+    seis_device_status instead of being read past the slot; the context stays usable."""
+    ns = seis.SEIS_MAX_TRACE_SAMPLES
+    rng = np.random.default_rng(9)
+    ds = dataset([rng.standard_normal(ns), rng.standard_normal(ns)], [20000.0, 20000.0], 0.001)
+    C = np.float32(np.linspace(0.0, 4e-6, 8))
+    seis.device_status()
+    g = seis.to_device(ds)
+    seis.cmp_semblance(g, torch.from_numpy(C).cuda(), w=11)
+    torch.cuda.synchronize()
+    with pytest.raises(seis.SeisError) as e:
+        seis.device_status()
+    assert e.value.code == seis.SEIS_EUNSUPPORTED
+    seis.device_status()                                   # cleared
+    _check_all(seis, synth.cmp_line(2, 6, 200, 0.004, 0.0, 1000.0, 2, 2.0, seed=3), _grid(9),
+               label="after overflow")
