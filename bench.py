@@ -449,15 +449,17 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
         seis.autotune_clear()
         seis.set_search_variant(args.variant)
         chosen, tune_ms = args.variant, []
-    seis.crs_semblance(g, ap, A, B, C, w=W)
+    split = getattr(args, "split", False)
+    seis.crs_semblance(g, ap, A, B, C, w=W, split=split)
     for _ in range(args.warmup - 1):
-        seis.crs_semblance(g, ap, A, B, C, w=W)
+        seis.crs_semblance(g, ap, A, B, C, w=W, split=split)
     torch.cuda.synchronize()
     seis.device_status()
     clocks = ClockSampler(dev.index)
     clocks.start()
     kern, total = _time_steps(torch, torch.cuda.current_stream(),
-                              lambda: seis.crs_semblance(g, ap, A, B, C, w=W), args.steps)
+                              lambda: seis.crs_semblance(g, ap, A, B, C, w=W, split=split),
+                              args.steps)
     clk = clocks.stop()
     ms = _max_over_ranks(torch, dist, world, dev, total / args.steps)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -483,7 +485,8 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
                                      "+-10 CMPs (1008 traces), 1500 samples @4ms, 21x21x41, w=11",
                          "intersections_per_step": inter * world, "kernel_variant": chosen,
                          "kernel_variant_name": seis.search_variants()[chosen],
-                         "autotune_ms_4_centrals": [round(x, 3) for x in tune_ms]},
+                         "autotune_ms_4_centrals": [round(x, 3) for x in tune_ms],
+                         "split_candidates_over_ctas": bool(split)},
                         {"intersections_per_s": inter * world / (ms / 1e3),
                          "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
                                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
@@ -984,6 +987,9 @@ def main():
                     help="refine: starts at the coarse cube's best local maxima or its best "
                          "candidates")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs only")
+    ap.add_argument("--split", action="store_true",
+                    help="crs-line: spread each tile's candidates over several CTAs when the "
+                         "centrals do not fill the GPU (crs_semblance_ws)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="cmp-line: leave out the crs and refine sub-objects")
     ap.add_argument("--variant", type=int, default=None,

@@ -225,6 +225,34 @@ int seis_crs_aperture_offset(const seis_gathers* d, const int32_t* central, int6
                              int64_t* total_entries, int64_t* total_rows, int32_t* max_rows,
                              void* stream);
 
+/* The searches for problems too small to fill the GPU (no counterpart in the paper, whose
+ * CGs take one CDP each, Section 3.5).  A search launches one CTA per (gather or central
+ * CDP, tile of 32 output rows), so a few owners leave most SMs idle, and a grid just past a
+ * whole number of waves leaves a last wave nearly empty.  These entry points split each
+ * tile's candidates over the fewest CTAs that keep at least 90 % of the launch's waves
+ * occupied (two CTAs per SM), each CTA writing the argmax of its own candidates to the
+ * workspace, and merge the parts per row (the earlier part on ties).  A split launch uses
+ * the default kernel variant (4) whatever the autotuner recorded.  Every output is
+ * bit-identical to cmp_semblance / crs_semblance; with enough tiles they run exactly those.
+ *   workspace: device scratch of seis_search_workspace_size(n_owner, max_rows, rows, ncand)
+ *   bytes (0 when no split is needed; then workspace may be NULL), 16-byte aligned,
+ *   caller-owned; n_owner = ngathers (CMP) or ap->n_central (CRS), max_rows and ncand as in
+ *   the call, rows (host) = the number of output rows (out_off[n_owner]).  The split depends
+ *   on the current device's SM count.
+ * Other arguments, outputs and errors as cmp_semblance / crs_semblance, and SEIS_EINVAL
+ * when the workspace is too small. */
+size_t seis_search_workspace_size(int64_t n_owner, int32_t max_rows, int64_t rows,
+                                  int64_t ncand);
+int cmp_semblance_ws(const seis_gathers* d, const float* C, int32_t nc, int32_t w,
+                     float* S_cube, int32_t* best_idx, float* best_C, float* best_S,
+                     float* stack_out, void* workspace, size_t ws_bytes, int64_t rows,
+                     void* stream);
+int crs_semblance_ws(const seis_gathers* d, const seis_aperture* ap, const float* A,
+                     int32_t nA, const float* B, int32_t nB, const float* C, int32_t nC,
+                     int32_t w, float* S_cube, int32_t* best_idx, float* best_ABC,
+                     float* best_S, float* stack_out, void* workspace, size_t ws_bytes,
+                     int64_t rows, void* stream);
+
 /* CRS semblance search -- Section 2.2, Section 3.5 (aperture), Eq. 1, Algorithm 1.
  * Candidates are the flattened grid cand = (ia*nB + ib)*nC + ic of A[nA] (s/m),
  * B[nB] (s^2/m^2), C[nC] (s^2/m^2); trace i of the aperture of central c is intersected

@@ -703,7 +703,9 @@ __device__ __forceinline__ void reduce_best(const SearchSmem& sm, int nwarps, in
     if (bc == INT_MAX) { bc = 0; bs = 0.f; bt = 0.f; }
 }
 
-template <bool CRS, int W, class CFG>
+// SPLIT: the CTAs of a tile share its candidate passes (P.nsplit parts, partial argmaxes to
+// P.partial, merged by merge_partials_kernel); without it the kernel ignores both fields.
+template <bool CRS, int W, class CFG, bool SPLIT = false>
 __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchParams P) {
     constexpr int HW = W / 2;
     constexpr int kWarps = CFG::kWarps;
@@ -715,8 +717,11 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t owner = blockIdx.x / P.tiles_per_owner;
-    const int tile = (int)(blockIdx.x - owner * P.tiles_per_owner);
+    // CTA = (owner, tile of 32 rows[, part of the candidate passes])
+    const unsigned otile = SPLIT ? blockIdx.x / (unsigned)P.nsplit : blockIdx.x;
+    const int part = SPLIT ? (int)(blockIdx.x - otile * (unsigned)P.nsplit) : 0;
+    const int64_t owner = otile / P.tiles_per_owner;
+    const int tile = (int)(otile - owner * P.tiles_per_owner);
     if (owner >= P.nowner) return;
     const int64_t row0 = P.out_off[owner];
     const int nrows = (int)(P.out_off[owner + 1] - row0);
@@ -726,7 +731,10 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
     const int64_t M64 = P.list_off[owner + 1] - lbeg;
     const int M = M64 < 0 ? 0 : (M64 > INT_MAX ? INT_MAX : (int)M64);
     const float dt = P.dt[owner];
-    const int npass = (P.ncand + kCB - 1) / kCB;
+    const int npass_all = (P.ncand + kCB - 1) / kCB;
+    const int pass_begin = SPLIT ? (int)((int64_t)part * npass_all / P.nsplit) : 0;
+    const int npass = SPLIT ? (int)((int64_t)(part + 1) * npass_all / P.nsplit)
+                            : npass_all;                         // passes [begin, npass)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSlots; ++s) {
@@ -743,7 +751,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
         // =============================== producer warp ================================
         const float mc = CRS ? P.m_c[owner] : 0.f;
         const int n_last = min(n0 + 31, nrows - 1);
-        int pl_pass = 0, pl_t = 0, pl_bpass = -1;
+        int pl_pass = pass_begin, pl_t = 0, pl_bpass = -1;
         float bA0 = 0.f, bA1 = 0.f, bB0 = 0.f, bB1 = 0.f, bC0 = 0.f, bC1 = 0.f;
         int s = 0;
         for (;; ++s) {
@@ -841,6 +849,10 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
         int bc;
         reduce_best(sm, kWarps, lane, bs, bc, bt);
         const int64_t row = row0 + n;
+        if constexpr (SPLIT) {                        // one part of a split tile
+            P.partial[row * P.nsplit + part] = make_float4(bs, __int_as_float(bc), bt, 0.f);
+            return;
+        }
         P.best_idx[row] = bc;
         P.best_S[row] = bs;
         P.stack[row] = bt;
@@ -858,7 +870,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
     }
 }
 
-template <bool CRS, int W, class CFG>
+template <bool CRS, int W, class CFG, bool SPLIT = false>
 cudaError_t launch_search_w(const SearchParams& p, cudaStream_t stream) {
     static bool configured[64] = {};  // dynamic shared-memory opt-in, once per device
     const int smem = (int)sizeof(SearchSmem);
@@ -866,29 +878,30 @@ cudaError_t launch_search_w(const SearchParams& p, cudaStream_t stream) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(search_kernel<CRS, W, CFG>,
+        e = cudaFuncSetAttribute(search_kernel<CRS, W, CFG, SPLIT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = true;
     }
-    const int64_t grid = p.nowner * (int64_t)p.tiles_per_owner;
+    const int64_t parts = SPLIT ? p.nsplit : 1;
+    const int64_t grid = p.nowner * (int64_t)p.tiles_per_owner * parts;
     if (grid <= 0) return cudaSuccess;
-    if (grid > INT_MAX) return cudaErrorInvalidValue;
-    search_kernel<CRS, W, CFG><<<(unsigned)grid, CFG::kThreads, smem, stream>>>(p);
+    if (grid > INT_MAX || parts < 1) return cudaErrorInvalidValue;
+    search_kernel<CRS, W, CFG, SPLIT><<<(unsigned)grid, CFG::kThreads, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
-template <bool CRS, class CFG>
+template <bool CRS, class CFG, bool SPLIT = false>
 cudaError_t launch_search_cfg(const SearchParams& p, int w, cudaStream_t stream) {
     switch (w) {
-        case 1: return launch_search_w<CRS, 1, CFG>(p, stream);
-        case 3: return launch_search_w<CRS, 3, CFG>(p, stream);
-        case 5: return launch_search_w<CRS, 5, CFG>(p, stream);
-        case 7: return launch_search_w<CRS, 7, CFG>(p, stream);
-        case 9: return launch_search_w<CRS, 9, CFG>(p, stream);
-        case 11: return launch_search_w<CRS, 11, CFG>(p, stream);
-        case 13: return launch_search_w<CRS, 13, CFG>(p, stream);
-        case 15: return launch_search_w<CRS, 15, CFG>(p, stream);
+        case 1: return launch_search_w<CRS, 1, CFG, SPLIT>(p, stream);
+        case 3: return launch_search_w<CRS, 3, CFG, SPLIT>(p, stream);
+        case 5: return launch_search_w<CRS, 5, CFG, SPLIT>(p, stream);
+        case 7: return launch_search_w<CRS, 7, CFG, SPLIT>(p, stream);
+        case 9: return launch_search_w<CRS, 9, CFG, SPLIT>(p, stream);
+        case 11: return launch_search_w<CRS, 11, CFG, SPLIT>(p, stream);
+        case 13: return launch_search_w<CRS, 13, CFG, SPLIT>(p, stream);
+        case 15: return launch_search_w<CRS, 15, CFG, SPLIT>(p, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -98,6 +98,8 @@ int build_cmp_params(const seis_gathers* d, const float* C, int32_t nc, int32_t 
     p.best_S = best_S;
     p.stack = stack_out;
     p.status = device_status_word();
+    p.nsplit = 1;
+    p.partial = nullptr;
     *key = make_tune_key(false, w, nc, d->max_rows, d->ntraces / d->ngathers);
     p.variant = lookup_variant(*key, default_variant());
     *out = p;
@@ -145,6 +147,8 @@ int build_crs_params(const seis_gathers* d, const seis_aperture* ap, const float
     p.best_S = best_S;
     p.stack = stack_out;
     p.status = device_status_word();
+    p.nsplit = 1;
+    p.partial = nullptr;
     *key = make_tune_key(true, w, (int)ncand, ap->max_rows, 0);
     p.variant = lookup_variant(*key, default_variant());
     *out = p;

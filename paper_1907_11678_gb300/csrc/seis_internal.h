@@ -39,6 +39,11 @@ struct SearchParams {
     float* stack;
     unsigned* status;
     int variant;               // search kernel variant (tile shape / arithmetic form)
+    // candidate passes of each tile split over nsplit CTAs (1: no split); with nsplit > 1 the
+    // CTAs write their partial argmax to partial[row * nsplit + part] (best S, candidate,
+    // stack) and merge_partials_kernel forms the outputs
+    int nsplit;
+    float4* partial;
 };
 
 struct EvalParams {
@@ -85,6 +90,7 @@ struct RefineParams {
 
 // Launchers (return the cudaError_t of the launch).
 cudaError_t launch_search(const SearchParams& p, bool crs, int w, cudaStream_t stream);
+cudaError_t launch_merge_partials(const SearchParams& p, bool crs, int64_t rows, cudaStream_t s);
 cudaError_t launch_eval(const EvalParams& p, bool crs, bool grad, int w, cudaStream_t s);
 cudaError_t launch_refine_update(const RefineParams& r, cudaStream_t s);
 int refine_run(const EvalParams& p0, float* theta, const float* lo3, const float* hi3,

@@ -69,6 +69,12 @@ def load_library(path: str | None = None):
             lib.crs_semblance.argtypes = [vp, vp, vp, i32, vp, i32, vp, i32, i32,
                                           vp, vp, vp, vp, vp, vp]
             lib.crs_semblance_t0win.argtypes = lib.crs_semblance.argtypes
+            lib.seis_search_workspace_size.argtypes = [i64, i32, i64, i64]
+            lib.seis_search_workspace_size.restype = ctypes.c_size_t
+            lib.cmp_semblance_ws.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp,
+                                             ctypes.c_size_t, i64, vp]
+            lib.crs_semblance_ws.argtypes = [vp, vp, vp, i32, vp, i32, vp, i32, i32,
+                                             vp, vp, vp, vp, vp, vp, ctypes.c_size_t, i64, vp]
             lib.seis_crs_aperture.argtypes = [vp, vp, i64, f32, vp, vp, i64, vp, vp, vp,
                                               vp, vp, vp, vp]
             lib.seis_search_variant_name.restype = ctypes.c_char_p
@@ -118,6 +124,7 @@ def load_library(path: str | None = None):
                          "crs_refine_multi", "seis_batch_semblance", "seis_autotune_batch",
                          "seis_crs_aperture_offset", "crs_pragmatic", "cmp_semblance_t0win",
                          "crs_semblance_t0win", "seis_velocity_grid", "seis_linear_grid",
+                         "cmp_semblance_ws", "crs_semblance_ws",
                          "seis_selftest_fast_math",
                          "seis_selftest_wait_timeout"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -279,10 +286,18 @@ def linear_grid(lo: float, hi: float, n: int, device="cuda", stream=None) -> tor
     return out
 
 
+def _split_workspace(lib, dev, n_owner: int, max_rows: int, rows: int, ncand: int):
+    """The scratch a split search needs on this device (None when it needs none)."""
+    n = lib.seis_search_workspace_size(n_owner, max_rows, rows, ncand)
+    return None if n == 0 else torch.empty(n, dtype=torch.uint8, device=dev)
+
+
 def cmp_semblance(g: Gathers, C: torch.Tensor, w: int = 11, want_cube: bool = False,
-                  stream=None, out: dict | None = None) -> dict:
+                  stream=None, out: dict | None = None, split: bool = False) -> dict:
     """CMP semblance search (include/seis.h: cmp_semblance).  Returns device tensors
-    best_idx, best_C, best_S, stack (and S [rows, nc] when want_cube)."""
+    best_idx, best_C, best_S, stack (and S [rows, nc] when want_cube).  split: spread each
+    tile's candidates over several CTAs when the gathers do not fill the GPU
+    (cmp_semblance_ws; bit-identical results)."""
     lib = load_library()
     dev = g.traces.device
     C = _input(C, "C", dev)
@@ -293,9 +308,17 @@ def cmp_semblance(g: Gathers, C: torch.Tensor, w: int = 11, want_cube: bool = Fa
             out["S"] = torch.empty((g.rows, nc), dtype=torch.float32, device=dev)
     else:
         _check_rows_out(out, dev, g.rows, nc, abc=False)
-    rc = lib.cmp_semblance(ctypes.byref(g.descriptor()), _ptr(C), nc, w, _ptr(out.get("S")),
-                           _ptr(out["best_idx"]), _ptr(out.get("best_C")), _ptr(out["best_S"]),
-                           _ptr(out["stack"]), _stream_handle(stream))
+    if split:
+        ws = _split_workspace(lib, dev, g.ngathers, g.max_rows, g.rows, nc)
+        rc = lib.cmp_semblance_ws(ctypes.byref(g.descriptor()), _ptr(C), nc, w,
+                                  _ptr(out.get("S")), _ptr(out["best_idx"]),
+                                  _ptr(out.get("best_C")), _ptr(out["best_S"]), _ptr(out["stack"]),
+                                  _ptr(ws), 0 if ws is None else ws.numel(), g.rows,
+                                  _stream_handle(stream))
+    else:
+        rc = lib.cmp_semblance(ctypes.byref(g.descriptor()), _ptr(C), nc, w, _ptr(out.get("S")),
+                               _ptr(out["best_idx"]), _ptr(out.get("best_C")),
+                               _ptr(out["best_S"]), _ptr(out["stack"]), _stream_handle(stream))
     _check(rc)
     return out
 
@@ -374,7 +397,7 @@ def crs_aperture(g: Gathers, central, apm: float, hmax: float | None = None,
     return Aperture(nbr_off, nbr_trace, m_c, out_off, dt_c, n, int(mr.value), int(rows.value))
 
 
-def _crs_search(lib_fn, g, ap, A, B, C, w, want_cube, stream, out=None) -> dict:
+def _crs_search(lib_fn, g, ap, A, B, C, w, want_cube, stream, out=None, split=False) -> dict:
     lib = load_library()
     dev = g.traces.device
     A, B, C = _input(A, "A", dev), _input(B, "B", dev), _input(C, "C", dev)
@@ -385,20 +408,27 @@ def _crs_search(lib_fn, g, ap, A, B, C, w, want_cube, stream, out=None) -> dict:
             out["S"] = torch.empty((ap.rows, nA * nB * nC), dtype=torch.float32, device=dev)
     else:
         _check_rows_out(out, dev, ap.rows, nA * nB * nC, abc=True)
-    rc = getattr(lib, lib_fn)(ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()),
-                              _ptr(A), nA, _ptr(B), nB, _ptr(C), nC, w, _ptr(out.get("S")),
-                              _ptr(out["best_idx"]), _ptr(out["best_ABC"]), _ptr(out["best_S"]),
-                              _ptr(out["stack"]), _stream_handle(stream))
+    args = (ctypes.byref(g.descriptor()), ctypes.byref(ap.descriptor()), _ptr(A), nA, _ptr(B),
+            nB, _ptr(C), nC, w, _ptr(out.get("S")), _ptr(out["best_idx"]), _ptr(out["best_ABC"]),
+            _ptr(out["best_S"]), _ptr(out["stack"]))
+    if split:
+        ws = _split_workspace(lib, dev, ap.n_central, ap.max_rows, ap.rows, nA * nB * nC)
+        rc = lib.crs_semblance_ws(*args, _ptr(ws), 0 if ws is None else ws.numel(), ap.rows,
+                                  _stream_handle(stream))
+    else:
+        rc = getattr(lib, lib_fn)(*args, _stream_handle(stream))
     _check(rc)
     return out
 
 
 def crs_semblance(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor,
-                  w: int = 11, want_cube: bool = False, stream=None, out: dict | None = None) -> dict:
+                  w: int = 11, want_cube: bool = False, stream=None, out: dict | None = None,
+                  split: bool = False) -> dict:
     """CRS semblance search over the flattened A x B x C grid (include/seis.h:
     crs_semblance).  Returns best_idx, best_ABC [rows, 3], best_S, stack (and S); `out`
-    supplies the output tensors instead (as cmp_semblance)."""
-    return _crs_search("crs_semblance", g, ap, A, B, C, w, want_cube, stream, out)
+    supplies the output tensors instead (as cmp_semblance); split as cmp_semblance
+    (crs_semblance_ws)."""
+    return _crs_search("crs_semblance", g, ap, A, B, C, w, want_cube, stream, out, split)
 
 
 def crs_semblance_t0win(g: Gathers, ap: Aperture, A: torch.Tensor, B: torch.Tensor,

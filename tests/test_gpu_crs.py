@@ -1,5 +1,7 @@
 """CRS aperture build and CRS semblance search on the GPU (through the C ABI) against
 the FP64 oracle."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -215,3 +217,55 @@ def test_crs_t0win_matches_oracle(seis, w):
     ia, rem = np.divmod(got["best_idx"], 3 * 7)
     ib, ic = np.divmod(rem, 7)
     np.testing.assert_array_equal(got["best_ABC"], np.stack([A[ia], B[ib], C[ic]], 1))
+
+
+# --- problems too small to fill the GPU: candidate passes split over CTAs ----------------
+
+def test_split_search_is_bitwise_identical(seis):
+    """Two central CMPs (fewer tiles than one wave of the GPU): crs_semblance_ws spreads each
+    tile's candidates over several CTAs and merges their argmaxes; every output, the cube
+    included, equals crs_semblance's bit for bit, and matches the oracle."""
+    ds = synth.crs_line(9, 12, 330, 0.004, 0.0, 1500.0, 2, 1, 2.0, seed=141)
+    g = seis.to_device(ds)
+    ap = seis.crs_aperture(g, [3, 5], 30.0)
+    A, B, C = _grids(7, 5, 13)
+    lib = seis.load_library()
+    assert lib.seis_search_workspace_size(ap.n_central, ap.max_rows, ap.rows, 7 * 5 * 13) > 0
+    t = lambda a: torch.from_numpy(np.asarray(a, np.float32)).cuda()
+    one = seis.crs_semblance(g, ap, t(A), t(B), t(C), w=11, want_cube=True)
+    split = seis.crs_semblance(g, ap, t(A), t(B), t(C), w=11, want_cube=True, split=True)
+    torch.cuda.synchronize()
+    seis.device_status()
+    for k in one:
+        assert torch.equal(one[k], split[k]), k
+    ref = oracle.crs_semblance(ds, oracle.aperture(ds, [3, 5], 30.0), A, B, C, want_cube=True)
+    got = {k: v.cpu().numpy() for k, v in split.items()}
+    parity.check_cube(got["S"], ref, "crs split")
+    parity.check_picks(got["best_idx"], got["best_S"], got["stack"], ref, "crs split")
+
+
+def test_split_cmp_and_large_problems(seis):
+    """CMP: one gather of 300 rows (ten tiles) split, bit-identical to cmp_semblance; a
+    workload with a full wave of tiles needs no workspace and takes the plain path; a
+    workspace that is too small is refused."""
+    lib = seis.load_library()
+    ds = synth.cmp_line(1, 20, 300, 0.004, 0.0, 1500.0, 3, 2.0, seed=142)
+    g = seis.to_device(ds)
+    C = torch.from_numpy(_grids(1, 1, 201)[2]).cuda()
+    one = seis.cmp_semblance(g, C, w=11, want_cube=True)
+    split = seis.cmp_semblance(g, C, w=11, want_cube=True, split=True)
+    torch.cuda.synchronize()
+    seis.device_status()
+    for k in one:
+        assert torch.equal(one[k], split[k]), k
+    assert lib.seis_search_workspace_size(4096, 2000, 4096 * 2000, 201) == 0
+    need = lib.seis_search_workspace_size(g.ngathers, g.max_rows, g.rows, 201)
+    assert need > 0
+    ws = torch.empty(need - 16, dtype=torch.uint8, device="cuda")
+    out = seis._rows_out(g.traces.device, g.rows, abc=False)
+    P = seis._ptr
+    rc = lib.cmp_semblance_ws(ctypes.byref(g.descriptor()), P(C), 201, 11, None,
+                              P(out["best_idx"]), P(out["best_C"]), P(out["best_S"]),
+                              P(out["stack"]), P(ws), ws.numel(), g.rows,
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == seis.SEIS_EINVAL and "workspace" in lib.seis_last_error().decode()
