@@ -595,6 +595,20 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
     search_ms = float(np.mean(kern)) - multi_ms       # coarse search + start selection
     coarse, ref = refine_all()
     one = seis.crs_refine(g, ap, coarse["best_ABC"], lo, hi, steps=steps, step0=0.05, w=W)
+    # a second, smaller start count timed the same way (quality against time)
+    few = None
+    if args.refine_also_starts and args.refine_also_starts != nstart:
+        k2 = args.refine_also_starts
+
+        def refine_few():
+            c2 = seis.crs_semblance(g, ap, A7, B7, C11, w=W, want_cube=True)
+            st2 = seis.crs_top_starts(c2["S"], A7, B7, C11, k2, local_max=local_max)
+            return seis.crs_refine_multi(g, ap, st2, lo, hi, steps=steps, step0=0.05, w=W,
+                                         workspace=ws)
+        refine_few()
+        torch.cuda.synchronize()
+        _, tot2 = _time_steps(torch, stream, refine_few, args.steps)
+        few = (k2, tot2 / args.steps, refine_few())
     # the other start rule, untimed, for comparison (optional: it repeats the refinement)
     other = None
     if args.compare_start_rules:
@@ -659,6 +673,9 @@ def run_refine(args, torch, dist, seis, synth, rank, world, dev):
                          "one_start (untimed, for comparison)": quality(one["S"]),
                          **({f"start rule {'top' if local_max else 'localmax'} (untimed, for comparison)":
                              quality(other["S"])} if other is not None else {}),
+                         **({f"{few[0]} starts (timed the same way)":
+                             {"refine_ms": few[1], "speedup_refine_vs_dense": dense_ms / few[1],
+                              **quality(few[2]["S"])}} if few is not None else {}),
                          "mean_S_gain_over_coarse": float((ref["S"] - coarse["best_S"]).mean()),
                          "roofline": {"bound": "alu", "kernel": "eval_kernel<CRS, w=11, adjoint>",
                                       "achieved": ach_eval, "peak": peak, "unit": "TFLOP/s",
@@ -979,6 +996,8 @@ def main():
     ap.add_argument("--dense-centrals", type=int, default=24,
                     help="refine: dense-grid slice (24 x 63 tiles = 4.97 waves of 304 CTAs)")
     ap.add_argument("--starts", type=int, default=128, help="refine: coarse starts per row")
+    ap.add_argument("--refine-also-starts", type=int, default=16,
+                    help="refine: also time this start count (0: no)")
     ap.add_argument("--compare-start-rules", action="store_true",
                     help="refine: also report the other start rule's quality (untimed)")
     ap.add_argument("--coarse", default="7,7,11", help="refine: coarse grid nA,nB,nC")
