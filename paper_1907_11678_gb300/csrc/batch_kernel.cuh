@@ -76,14 +76,17 @@ __device__ __forceinline__ int64_t item_of_task_warp(const int64_t* task_off, in
 }
 
 // The search kernel's shared memory plus, per ring slot, the candidates of the pass that
-// the slot's stage starts and the task's sizes: the producer has them in registers when it
-// bounds the pass, so consumers take them from here instead of loading the item table and
-// the candidate pools from global memory at every pass (for small-fold items a pass is a
-// single stage of a few traces, and that latency would stall every warp once per stage).
+// the slot's stage starts: the producer has them in registers when it bounds the pass, so
+// consumers take them from here (and the task's sizes from the stage descriptor) instead of
+// loading the item table and the candidate pools from global memory at every pass (for
+// small-fold items a pass is a single stage of a few traces, and that latency would stall
+// every warp once per stage).  The consumers keep no per-task state in registers beyond
+// their row's constants: everything else comes with each stage.
 struct BatchSmem {
     SearchSmem s;
     float4 cand[kSlots][32];     // (A, B, C, -) of candidates pass * kCB + lane
-    int2 sizes[kSlots];          // (ncand, rows) of the stage's item
+    ItemView item;               // the producer's current item (read back as needed, which
+                                 // keeps the producer warp's registers few)
 };
 
 template <int W, class CFG>
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
     if (warp == kWarps) {
         // =============================== producer warp ================================
         bool have = false;
-        ItemView it{};
+        const ItemView& it = bsm.item;
         int64_t item = 0;
         // the next task is claimed one task ahead, so the atomic's latency passes while the
         // current task's stages are produced
@@ -144,7 +147,8 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
                     if (lane == 0) next = atomicAdd(P.counter, 1ull);
                     item = item_of_task_warp(P.task_off, P.item_begin, P.item_end, tk);
                     tile = (int)(tk - P.task_off[item]);
-                    it = load_item(P, item);
+                    if (lane == 0) bsm.item = load_item(P, item);
+                    __syncwarp();
                     n0 = tile * 32;
                     n_last = min(n0 + 31, it.nrows - 1);
                     npass = (it.ncand + kCB - 1) / kCB;
@@ -172,12 +176,12 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
                 pl_bpass = pl_pass;
                 // the pass's first stage carries its candidates (released with the stage)
                 bsm.cand[slot][lane] = make_float4(a, b, cc, 0.f);
-                if (lane == 0) bsm.sizes[slot] = make_int2(it.ncand, it.nrows);
             }
             int nfit = 0;
             unsigned allv = 0u;
             const int ntr = produce_stage<true, HW>(
-                sm.buf[slot], sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h,
+                sm.buf[slot], (int)(sm.buf[slot] - reinterpret_cast<float*>(smem_raw)),
+                sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h,
                 it.kind ? P.m : nullptr, nullptr, it.lbeg, it.M, pl_t, it.dt, it.mc, n0, n_last,
                 StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit, allv);
             pl_t += nfit;
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
             const int task_end = last && (pl_pass + 1 >= npass);
             if (lane == 0)
                 sm.desc[slot] = make_desc(pl_pass, ntr, allv, first, last, 0, (int)item, tile,
-                                          task_end);
+                                          task_end, it.ncand, it.nrows);
             if (last) { ++pl_pass; pl_t = 0; }
             __syncwarp();
             mbar_arrive(&sm.full[slot]);
@@ -197,38 +201,42 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
     }
 
     // ================================ consumer warps =====================================
+    // Loops nest as task > candidate pass > stage, so a pass's accumulators live only inside
+    // its loop and the task's argmax and outputs run with none of them held in registers.
+    // Every pass starts with its first stage (the producer bounds and stages passes in order).
     const float* smf = reinterpret_cast<const float*>(smem_raw);
     const int zidx = (int)(reinterpret_cast<const float*>(sm.zeros) - smf);
-    Accum<W, CFG> acc;
-    #pragma unroll
-    for (int r = 0; r < kR; ++r) acc.cidx[r] = INT_MAX;
-    int64_t task_item = 0;                       // the item of the current task
-    int ncand = 0;
-    RowConst rc = row_const(false, 0);
-    bool act = false;
-    int nrow = 0;
-    float bestS = -1.f, bestT = 0.f;
-    int bestC = INT_MAX;
-
-    for (int s = 0;; ++s) {
-        const int slot = s % kSlots;
-        if (!mbar_wait_bounded(&sm.full[slot], (uint32_t)((s / kSlots) & 1))) {
-            sm.abort_flag = 1;
-            record_status(P.status, kStatusTimeout);
-            break;
-        }
-        const StageDesc d = sm.desc[slot];
-        if (d.end) break;
-        if (d.first) {
-            const int2 sz = bsm.sizes[slot];
-            ncand = sz.x;
-            if (d.pass == 0) {                   // a new task
-                task_item = d.item;
-                nrow = d.tile * 32 + lane;
-                act = nrow < sz.y;
-                rc = row_const(act, nrow);
+    // the running best of this thread's row stays in its own entry of the reduction arrays
+    // (updated once per pass), which keeps three registers free for the trace loop
+    float& bestS = sm.redS[warp][lane];
+    int& bestC = sm.redC[warp][lane];
+    float& bestT = sm.redT[warp][lane];
+    int s = 0;                                    // the next stage
+    bool stop = false;
+    while (!stop) {                               // one task per iteration
+        bestS = -1.f;
+        bestC = INT_MAX;
+        bestT = 0.f;
+        int item = 0, tile = 0, nrows = 0;
+        bool task_end = false;
+        while (!task_end) {                       // one candidate pass per iteration
+            int slot = s % kSlots;
+            if (!mbar_wait_bounded(&sm.full[slot], (uint32_t)((s / kSlots) & 1))) {
+                sm.abort_flag = 1;
+                record_status(P.status, kStatusTimeout);
+                stop = true;
+                break;
             }
+            StageDesc d = sm.desc[slot];
+            if (d.end) {
+                stop = true;
+                break;
+            }
+            const int ncand = d.ncand;
+            const int nrow = d.tile * 32 + lane;
+            const RowConst rc = row_const(nrow < d.nrows, nrow);
             const int cbase = d.pass * kCB;
+            Accum<W, CFG> acc;
             const float4* cand = bsm.cand[slot];
             accum_begin(acc, cbase + warp * kR, ncand, [&](int c, float& a, float& b, float& cc) {
                 const float4 v = cand[c - cbase];
@@ -236,40 +244,58 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) batch_kernel(const BatchPara
                 b = v.y;
                 cc = v.z;
             });
-        }
-        const int ntr = min(d.ntr, kChunkT);
-        const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
-        if (ntr > 0 && acc.cidx[0] < ncand)
-            accum_stage<true, W, CFG>(acc, sm.meta[slot], ntr, d.allv, slot_base, rc, zidx, smf);
-        if (d.last) accum_end(acc, ncand, nullptr, bestS, bestC, bestT);
-        if (d.task_end) {                        // the task's last stage: argmax and outputs
-            const ItemView it = load_item(P, task_item);
-            sm.redS[warp][lane] = bestS;
-            sm.redC[warp][lane] = bestC;
-            sm.redT[warp][lane] = bestT;
-            consumer_bar(kConsumers);
-            if (warp == 0 && act) {
-                float bs, bt;
-                int bc;
-                reduce_best(sm, kWarps, lane, bs, bc, bt);
-                float a, b, cc;
-                decode_item(P, it, bc, a, b, cc);
-                const int64_t row = it.row0 + nrow;
-                P.best_idx[row] = bc;
-                P.best_S[row] = bs;
-                P.stack[row] = bt;
-                if (P.best_ABC) {
-                    P.best_ABC[row * 3 + 0] = a;
-                    P.best_ABC[row * 3 + 1] = b;
-                    P.best_ABC[row * 3 + 2] = cc;
+            // a warp whose candidates of this pass all lie past the end skips its stages
+            const bool live = acc.c0 < ncand;
+            for (;;) {                            // the pass's stages
+                const int ntr = min(d.ntr, kChunkT);
+                if (ntr > 0 && live)
+                    accum_stage<true, W, CFG>(acc, sm.meta[slot], ntr, d.allv, rc, zidx, smf);
+                const bool last = d.last != 0;
+                task_end = d.task_end != 0;
+                item = d.item;
+                tile = d.tile;
+                nrows = d.nrows;
+                mbar_arrive(&sm.empty[slot]);     // this thread is done with the slot
+                ++s;
+                if (last) break;
+                slot = s % kSlots;
+                if (!mbar_wait_bounded(&sm.full[slot], (uint32_t)((s / kSlots) & 1))) {
+                    sm.abort_flag = 1;
+                    record_status(P.status, kStatusTimeout);
+                    stop = true;
+                    break;
+                }
+                d = sm.desc[slot];
+                if (d.end) {                      // the producer gave up mid-pass
+                    stop = true;
+                    break;
                 }
             }
-            consumer_bar(kConsumers);            // the reduction arrays are free again
-            bestS = -1.f;
-            bestT = 0.f;
-            bestC = INT_MAX;
+            if (stop) break;
+            accum_end(acc, ncand, nullptr, bestS, bestC, bestT);
         }
-        mbar_arrive(&sm.empty[slot]);
+        if (stop) break;
+        // the task's last stage is done: argmax over the warps and outputs
+        consumer_bar(kConsumers);
+        const int nrow = tile * 32 + lane;
+        if (warp == 0 && nrow < nrows) {
+            const ItemView it = load_item(P, item);
+            float bs, bt;
+            int bc;
+            reduce_best(sm, kWarps, lane, bs, bc, bt);
+            float a, b, cc;
+            decode_item(P, it, bc, a, b, cc);
+            const int64_t row = it.row0 + nrow;
+            P.best_idx[row] = bc;
+            P.best_S[row] = bs;
+            P.stack[row] = bt;
+            if (P.best_ABC) {
+                P.best_ABC[row * 3 + 0] = a;
+                P.best_ABC[row * 3 + 1] = b;
+                P.best_ABC[row * 3 + 2] = cc;
+            }
+        }
+        consumer_bar(kConsumers);                 // the reduction arrays are free again
     }
 }
 

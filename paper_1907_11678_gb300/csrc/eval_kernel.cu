@@ -110,8 +110,9 @@ __global__ void __launch_bounds__(kEvalThreads, kEvalCTAs) eval_kernel(const Eva
             }
             int nfit = 0;
             unsigned allv = 0u;                 // unused: this kernel checks every pair
-            const int ntr = produce_stage<CRS, HW>(sm.buf[slot], sm.meta[slot], &sm.full[slot],
-                                                   P.traces, P.trace_off, P.h, P.m, P.list, lbeg,
+            const int ntr = produce_stage<CRS, HW>(sm.buf[slot], (int)(sm.buf[slot] - smf),
+                                                   sm.meta[slot], &sm.full[slot], P.traces,
+                                                   P.trace_off, P.h, P.m, P.list, lbeg,
                                                    M, pl_t, dt, mc, n0, n_last, bnd, P.status,
                                                    nfit, allv);
             pl_t += nfit;
@@ -161,9 +162,8 @@ __global__ void __launch_bounds__(kEvalThreads, kEvalCTAs) eval_kernel(const Eva
             break;
         }
         const int ntr = min(d.ntr, kChunkT);
-        const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
         for (int t = 0; t < ntr; ++t) {
-            const TraceConst tc = trace_const(sm.meta[slot][t], n, slot_base, HW);
+            const TraceConst tc = trace_const(sm.meta[slot][t], n);
             // traveltime (as the search kernel) plus, for the adjoint, du/d(A,B,C)
             float D, s_u, pp = nf;
             bool p_ok = true;

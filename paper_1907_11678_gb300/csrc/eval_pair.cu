@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
             }
             int nfit = 0;
             unsigned allv = 0u;                 // unused: every pair is checked
-            const int ntr = produce_stage<true, HW>(sm.buf[slot], sm.meta[slot], &sm.full[slot],
-                                                    P.traces, P.trace_off, P.h, P.m, P.list, lbeg,
+            const int ntr = produce_stage<true, HW>(sm.buf[slot], (int)(sm.buf[slot] - smf),
+                                                    sm.meta[slot], &sm.full[slot], P.traces,
+                                                    P.trace_off, P.h, P.m, P.list, lbeg,
                                                     M, pl_t, dt, mc, n0, n_last, bnd, P.status,
                                                     nfit, allv);
             pl_t += nfit;
@@ -159,14 +160,13 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
             break;
         }
         const int ntr = min(d.ntr, kChunkT);
-        const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
         for (int t = 0; t < ntr; ++t) {
-            const TraceConst tc = trace_const(sm.meta[slot][t], n, slot_base, HW);
+            const TraceConst tc = trace_const(sm.meta[slot][t], n);
             // traveltime of both operators (the single kernel's operations, lane-wise)
-            const f2_t e2 = pk2(tc.e, tc.e);
+            const f2_t e2 = tc.e2;
             const f2_t a2 = mul2(A2, e2);
             const f2_t pp2 = add2(nf2, a2);
-            const f2_t rr2 = fma2(B2, pk2(tc.g, tc.g), mul2(C2, pk2(tc.q, tc.q)));
+            const f2_t rr2 = fma2(B2, tc.g2, mul2(C2, tc.q2));
             const f2_t rad2 = fma2(pp2, pp2, rr2);
             float ra, rb, pa, pb;
             up2(rad2, ra, rb);

@@ -70,14 +70,18 @@ struct SearchCfg {
     static_assert(!kPairs || (R % 2) == 0, "candidate pairs need an even R");
 };
 
+// Per-trace metadata of one stage, written by the producer in the form the consumers use
+// directly: the index arithmetic is folded into three integers, and the geometry factors
+// are stored twice so that a packed f32x2 pair loads straight into a register pair.
 struct __align__(16) TraceMeta {
-    int base;     // shared-memory float index of sample 0 of the trace in its slot buffer
-    int kmin;     // intersections with kmin <= k <= kmax take part (window inside the trace
-    int kmax;     //   and inside the staged sample window)
-    float q;      // (h/dt)^2
-    float e;      // dm/dt            (CRS)
-    float g;      // (dm/dt)^2        (CRS)
-    int pad0, pad1;
+    int kbase;      // shared-memory float index of the window of k = kmin (slot included)
+    int offk;       // -(bits of the floor shift) - kmin: kk = bits(D + shift, rounded down)
+                    //   + n + offk, and intersections with 0 <= kk <= rng take part (window
+    unsigned rng;   //   inside the trace and inside the staged sample window); rng = kmax - kmin
+    int pad0;
+    float q, q_, e, e_;   // (h/dt)^2, dm/dt (CRS), each twice
+    float g, g_;          // (dm/dt)^2 (CRS), twice
+    int pad1, pad2;
 };
 
 struct __align__(16) StageDesc {
@@ -88,13 +92,14 @@ struct __align__(16) StageDesc {
     int end;           // no more stages
     int item, tile;    // batch kernel: the task
     int task_end;      // batch kernel: last stage of the task
-    int pad0, pad1, pad2;
+    int ncand, nrows;  // batch kernel: candidates and output rows of the task's item
+    int pad0;
 };
 
 __device__ __forceinline__ StageDesc make_desc(int pass, int ntr, unsigned allv, int first,
                                                int last, int end, int item = 0, int tile = 0,
-                                               int task_end = 0) {
-    return StageDesc{pass, ntr, allv, first, last, end, item, tile, task_end, 0, 0, 0};
+                                               int task_end = 0, int ncand = 0, int nrows = 0) {
+    return StageDesc{pass, ntr, allv, first, last, end, item, tile, task_end, ncand, nrows, 0};
 }
 
 struct SearchSmem {
@@ -193,23 +198,27 @@ __device__ __forceinline__ void decode_candidate(const SearchParams& P, int c, f
 }
 
 // Per-trace constants of one consumer thread: with kk = k - kmin, the trace takes part iff
-// 0 <= kk <= rng, and its window starts at shared-memory float index kbase + kk.
+// 0 <= kk <= rng, and its window starts at shared-memory float index kbase + kk.  q2, e2
+// and g2 hold each factor in both halves of a packed pair.
 struct TraceConst {
     float q, e, g;
+    f2_t q2, e2, g2;
     int off;        // n - kFloorShiftBits - kmin: kk = bits(D + shift, rounded down) + off
     unsigned rng;   // kmax - kmin
     int kbase;      // shared index of the window of k = kmin
 };
 
-__device__ __forceinline__ TraceConst trace_const(const TraceMeta& tm, int n, int slot_base,
-                                                  int hw) {
+__device__ __forceinline__ TraceConst trace_const(const TraceMeta& tm, int n) {
     TraceConst c;
     c.q = tm.q;
     c.e = tm.e;
     c.g = tm.g;
-    c.off = n - kFloorShiftBits - tm.kmin;
-    c.rng = (unsigned)(tm.kmax - tm.kmin);
-    c.kbase = slot_base + tm.base - hw + tm.kmin;
+    c.q2 = *reinterpret_cast<const f2_t*>(&tm.q);
+    c.e2 = *reinterpret_cast<const f2_t*>(&tm.e);
+    c.g2 = *reinterpret_cast<const f2_t*>(&tm.g);
+    c.off = n + tm.offk;
+    c.rng = tm.rng;
+    c.kbase = tm.kbase;
     return c;
 }
 
@@ -245,13 +254,13 @@ __device__ __forceinline__ void intersect_pair(f2_t A2, f2_t B2, f2_t C2, const 
                                                f2_t nf2, f2_t nsq2, int zidx,
                                                int& ia, int& ib, float& xa, float& xb,
                                                bool& oka, bool& okb) {
-    const f2_t q2 = pk2(tc.q, tc.q);
+    const f2_t q2 = tc.q2;
     f2_t D2;
     bool pa_ok = true, pb_ok = true;
     if (CRS) {
-        const f2_t a2 = mul2(A2, pk2(tc.e, tc.e));
+        const f2_t a2 = mul2(A2, tc.e2);
         const f2_t pp2 = add2(nf2, a2);
-        const f2_t rr2 = fma2(B2, pk2(tc.g, tc.g), mul2(C2, q2));
+        const f2_t rr2 = fma2(B2, tc.g2, mul2(C2, q2));
         const f2_t rad2 = fma2(pp2, pp2, rr2);
         float ra, rb, pa, pb;
         up2(rad2, ra, rb);
@@ -300,7 +309,8 @@ struct StageBounds {
 // most 3 head and 3 tail samples.  Empty windows are left out; the metadata of the others is
 // compacted into meta[0..ntr).  Returns ntr; nfit = traces consumed from the list.
 template <bool CRS, int HW>
-__device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, uint64_t* full,
+__device__ __forceinline__ int produce_stage(float* slotbuf, int slot_base, TraceMeta* meta,
+                                             uint64_t* full,
                                              const float* traces, const int64_t* trace_off,
                                              const float* hh, const float* mm, const int32_t* list,
                                              int64_t lbeg, int M, int pl_t, float dt, float mc,
@@ -315,7 +325,7 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
     int len = 0, n_el = 0, mis = 0, lo = 0;
     bool allv = false;
     const float* src = nullptr;
-    TraceMeta tm{0, 1, 0, 0.f, 0.f, 0.f, 0, 0};
+    TraceMeta tm{};
     if (v) {
         const int64_t tid = list ? (int64_t)list[lbeg + t] : (lbeg + t);
         const int64_t toff = trace_off[tid];
@@ -324,11 +334,12 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
         const double dtd = (double)dt;
         const double hd = (double)hh[tid];
         tm.q = (float)(hd * hd / (dtd * dtd));
+        tm.q_ = tm.q;
         float aLo = 0.f, aHi = 0.f, rLo, rHi;
         if (CRS) {
             const double dm = mm ? (double)mm[tid] - (double)mc : 0.0;   // no midpoints: CMP
-            tm.e = (float)(dm / dtd);
-            tm.g = (float)(dm * dm / (dtd * dtd));
+            tm.e = tm.e_ = (float)(dm / dtd);
+            tm.g = tm.g_ = (float)(dm * dm / (dtd * dtd));
             aLo = fminf(bA0 * tm.e, bA1 * tm.e);
             aHi = fmaxf(bA0 * tm.e, bA1 * tm.e);
             rLo = bB0 * tm.g + bC0 * tm.q;
@@ -352,8 +363,8 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
             allv = klo >= HW && khi <= ns_i - HW - 2 && (!CRS || (float)n0 + aLo >= 1e-3f) &&
                    radLo >= 1.f;
             if (kmin <= kmax) {
-                tm.kmin = kmin;
-                tm.kmax = kmax;
+                tm.offk = -kFloorShiftBits - kmin;
+                tm.rng = (unsigned)(kmax - kmin);
                 lo = kmin - HW;
                 n_el = (kmax + HW + 1) - lo + 1;
                 src = traces + toff + lo;
@@ -383,7 +394,7 @@ __device__ __forceinline__ int produce_stage(float* slotbuf, TraceMeta* meta, ui
         allv_out = 0u;
     } else if (lane < nfit && n_el > 0) {
         const int off = pre - len;                       // multiple of 4 floats
-        tm.base = off + mis - lo;
+        tm.kbase = slot_base + off + mis;      // the first staged sample, kmin - HW
         meta[pos] = tm;
         float* dst = slotbuf + off + mis;
         const int head = min((4 - mis) & 3, n_el);
@@ -427,12 +438,12 @@ template <bool CRS>
 __device__ __forceinline__ void intersect_pair_fast(f2_t A2, f2_t B2, f2_t C2, const TraceConst& tc,
                                                     f2_t nf2, f2_t nsq2, int& ia, int& ib,
                                                     f2_t& x2) {
-    const f2_t q2 = pk2(tc.q, tc.q);
+    const f2_t q2 = tc.q2;
     f2_t D2;
     if (CRS) {
-        const f2_t a2 = mul2(A2, pk2(tc.e, tc.e));
+        const f2_t a2 = mul2(A2, tc.e2);
         const f2_t pp2 = add2(nf2, a2);
-        const f2_t rr2 = fma2(B2, pk2(tc.g, tc.g), mul2(C2, q2));
+        const f2_t rr2 = fma2(B2, tc.g2, mul2(C2, q2));
         const f2_t rad2 = fma2(pp2, pp2, rr2);
         float ra, rb;
         up2(rad2, ra, rb);
@@ -474,7 +485,7 @@ struct Accum {
     int cntv[kR];
     float Ar[kR], Br[kR], Cr[kR];
     f2_t A2[kP ? kG : 1], B2[kP ? kG : 1], C2[kP ? kG : 1];
-    int cidx[kR];
+    int c0;                                          // candidates c0 .. c0 + kR - 1
 };
 
 // Row constants of one consumer thread.  Rows past the owner's end carry n = 2^24 so that
@@ -498,10 +509,10 @@ __device__ __forceinline__ RowConst row_const(bool act, int nrow) {
 // Start a pass: candidates c0 .. c0+kR-1 (those >= ncand are computed, then discarded).
 template <int W, class CFG, class Decode>
 __device__ __forceinline__ void accum_begin(Accum<W, CFG>& a, int c0, int ncand, Decode decode) {
+    a.c0 = c0;
     #pragma unroll
     for (int r = 0; r < CFG::kR; ++r) {
         const int c = c0 + r;
-        a.cidx[r] = c;
         a.Ar[r] = a.Br[r] = a.Cr[r] = 0.f;
         if (c < ncand) decode(c, a.Ar[r], a.Br[r], a.Cr[r]);
         a.cntv[r] = 0;
@@ -528,9 +539,7 @@ __device__ __forceinline__ void accum_begin(Accum<W, CFG>& a, int c0, int ncand,
 // chains) are formed while the window of trace t is accumulated.
 template <bool CRS, int W, class CFG, bool FAST>
 __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* meta, int t0, int t1,
-                                          int slot_base, const RowConst& rc, int zidx,
-                                          const float* smf) {
-    constexpr int HW = W / 2;
+                                          const RowConst& rc, int zidx, const float* smf) {
     constexpr int kR = CFG::kR;
     constexpr int kG = Accum<W, CFG>::kG;
     int sI[kR];
@@ -540,7 +549,7 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
     constexpr bool kX2 = FAST && CFG::kMode == kPacked;
     f2_t sX2[kX2 ? kG : 1];
     auto setup = [&](int t) {
-        const TraceConst tc = trace_const(meta[t], rc.n, slot_base, HW);
+        const TraceConst tc = trace_const(meta[t], rc.n);
         if constexpr (CFG::kMode == kPacked) {
             #pragma unroll
             for (int g = 0; g < kG; ++g) {
@@ -631,7 +640,7 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
 // the runs, so every tile shape gives bit-identical results.
 template <bool CRS, int W, class CFG>
 __device__ __forceinline__ void accum_stage(Accum<W, CFG>& a, const TraceMeta* meta, int ntr,
-                                            unsigned allv, int slot_base, const RowConst& rc,
+                                            unsigned allv, const RowConst& rc,
                                             int zidx, const float* smf) {
     int t = 0;
     while (t < ntr) {
@@ -639,8 +648,8 @@ __device__ __forceinline__ void accum_stage(Accum<W, CFG>& a, const TraceMeta* m
         const unsigned rest = (fast ? ~allv : allv) >> t;    // first trace of the other kind
         const int len = rest ? __ffs(rest) - 1 : 32;
         const int t1 = min(ntr, t + len);
-        if (fast) accum_run<CRS, W, CFG, true>(a, meta, t, t1, slot_base, rc, zidx, smf);
-        else accum_run<CRS, W, CFG, false>(a, meta, t, t1, slot_base, rc, zidx, smf);
+        if (fast) accum_run<CRS, W, CFG, true>(a, meta, t, t1, rc, zidx, smf);
+        else accum_run<CRS, W, CFG, false>(a, meta, t, t1, rc, zidx, smf);
         t = t1;
     }
 }
@@ -652,7 +661,7 @@ __device__ __forceinline__ void accum_end(const Accum<W, CFG>& a, int ncand, flo
                                           float& bestS, int& bestC, float& bestT) {
     #pragma unroll
     for (int r = 0; r < CFG::kR; ++r) {
-        const int c = a.cidx[r];
+        const int c = a.c0 + r;
         if (c >= ncand) continue;
         // the numerator is summed in the same chain order as the energy, so a lone
         // participating trace gives exactly S = 1
@@ -783,7 +792,8 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
             int nfit = 0;
             unsigned allv = 0u;
             const int ntr = produce_stage<CRS, HW>(
-                sm.buf[slot], sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h, P.m,
+                sm.buf[slot], (int)(sm.buf[slot] - reinterpret_cast<float*>(smem_raw)),
+                sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h, P.m,
                 P.list, lbeg, M, pl_t, dt, mc, n0, n_last,
                 StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit, allv);
             pl_t += nfit;
@@ -807,10 +817,13 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
     const RowConst rc = row_const(act, n0 + lane);
     const int n = rc.n;
     Accum<W, CFG> acc;
-    #pragma unroll
-    for (int r = 0; r < kR; ++r) acc.cidx[r] = INT_MAX;
-    float bestS = -1.f, bestT = 0.f;
-    int bestC = INT_MAX;
+    acc.c0 = INT_MAX;
+    // the running best of this thread's row over its candidates stays in its own entry of
+    // the reduction arrays (updated once per pass), which keeps three registers free for
+    // the trace loop
+    sm.redS[warp][lane] = -1.f;
+    sm.redC[warp][lane] = INT_MAX;
+    sm.redT[warp][lane] = 0.f;
     bool aborted = false;
     auto decode = [&](int c, float& a, float& b, float& cc) { decode_candidate<CRS>(P, c, a, b, cc); };
 
@@ -829,19 +842,16 @@ __global__ void __launch_bounds__(CFG::kThreads, 2) search_kernel(const SearchPa
         }
         if (d.first) accum_begin(acc, d.pass * kCB + warp * kR, P.ncand, decode);
         const int ntr = min(d.ntr, kChunkT);
-        const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
         // a warp whose candidates of this pass all lie past the end skips the stage
-        if (ntr > 0 && acc.cidx[0] < P.ncand)
-            accum_stage<CRS, W, CFG>(acc, sm.meta[slot], ntr, d.allv, slot_base, rc, zidx, smf);
+        if (ntr > 0 && acc.c0 < P.ncand)
+            accum_stage<CRS, W, CFG>(acc, sm.meta[slot], ntr, d.allv, rc, zidx, smf);
         if (d.last)
             accum_end(acc, P.ncand, (P.S_cube && act) ? P.S_cube + (row0 + n) * (int64_t)P.ncand
-                                                      : nullptr, bestS, bestC, bestT);
+                                                      : nullptr, sm.redS[warp][lane],
+                      sm.redC[warp][lane], sm.redT[warp][lane]);
         mbar_arrive(&sm.empty[slot]);                   // this thread is done with the slot
     }
 
-    sm.redS[warp][lane] = bestS;
-    sm.redC[warp][lane] = bestC;
-    sm.redT[warp][lane] = bestT;
     consumer_bar(kConsumers);
     if (aborted || sm.abort_flag) return;
     if (warp == 0 && act) {

@@ -48,18 +48,17 @@ struct TwRows {
 // traveltimes of trace t+1 are formed while trace t is interpolated.
 template <bool CRS, bool FAST>
 __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0, int t1,
-                                       int slot_base, const TwRows& rw, int zidx,
-                                       const float* smf) {
+                                       const TwRows& rw, int zidx, const float* smf) {
     int sI0[kTwR], sI1[kTwR];
     f2_t sX2[kTwR];
     bool sO0[kTwR], sO1[kTwR];
     const f2_t shift2 = pk2(kFloorShift, kFloorShift);
     auto setup = [&](int t) {
         const TraceMeta& tm = meta[t];
-        const unsigned rng = (unsigned)(tm.kmax - tm.kmin);
-        const int kbase = slot_base + tm.base + tm.kmin;
-        const int off0 = rw.n0 - kFloorShiftBits - tm.kmin;
-        const int off1 = rw.n1 - kFloorShiftBits - tm.kmin;
+        const unsigned rng = tm.rng;
+        const int kbase = tm.kbase;
+        const int off0 = rw.n0 + tm.offk;
+        const int off1 = rw.n1 + tm.offk;
         #pragma unroll
         for (int r = 0; r < kTwR; ++r) {
             f2_t D2;
@@ -238,7 +237,8 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
             int nfit = 0;
             unsigned allv = 0u;
             const int ntr = produce_stage<CRS, 0>(
-                sm.buf[slot], sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h,
+                sm.buf[slot], (int)(sm.buf[slot] - reinterpret_cast<float*>(smem_raw)),
+                sm.meta[slot], &sm.full[slot], P.traces, P.trace_off, P.h,
                 CRS ? P.m : nullptr, P.list, lbeg, M, pl_t, dt, mc, n_first, n_last,
                 StageBounds{bA0, bA1, bB0, bB1, bC0, bC1}, P.status, nfit, allv);
             pl_t += nfit;
@@ -302,7 +302,6 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
             }
         }
         const int ntr = min(d.ntr, kChunkT);
-        const int slot_base = (int)(reinterpret_cast<const float*>(sm.buf[slot]) - smf);
         if (ntr > 0 && a.cidx[0] < P.ncand) {
             int t = 0;
             while (t < ntr) {                          // runs of check-free / checked traces
@@ -310,8 +309,8 @@ __global__ void __launch_bounds__(kTwThreads, 2) t0win_kernel(const SearchParams
                 const unsigned rest = (fast ? ~d.allv : d.allv) >> t;
                 const int len = rest ? __ffs(rest) - 1 : 32;
                 const int t1 = min(ntr, t + len);
-                if (fast) tw_run<CRS, true>(a, sm.meta[slot], t, t1, slot_base, rw, zidx, smf);
-                else tw_run<CRS, false>(a, sm.meta[slot], t, t1, slot_base, rw, zidx, smf);
+                if (fast) tw_run<CRS, true>(a, sm.meta[slot], t, t1, rw, zidx, smf);
+                else tw_run<CRS, false>(a, sm.meta[slot], t, t1, rw, zidx, smf);
                 t = t1;
             }
         }
