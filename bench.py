@@ -536,6 +536,16 @@ def run_batch(args, torch, dist, seis, synth, rank, world, dev):
     torch.cuda.synchronize()
     per_item_ms = (time.perf_counter() - t0) * 1e3
     seis.device_status()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # the replayed graph is the task-table kernel (one CTA) and the persistent batch kernel:
+    # the step time is the batch kernel's to within the setup's few microseconds
+    ach = inter * FLOPS_PER_INTERSECTION / (total / args.steps / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None,
+            "flops_per_intersection": FLOPS_PER_INTERSECTION,
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {SM_MAX_MHZ:g} MHz",
+            "kernel": f"batch_kernel<w=11, variant {chosen}> (one persistent launch per step)"}
     return _simple_line("batched CMP+CRS " + METRIC, inter * world * W / (ms / 1e3), ms, args,
                         world,
                         {"workload": f"batch: {args.items} items (CMP p=0.5: 101-201 C; CRS "
@@ -545,9 +555,10 @@ def run_batch(args, torch, dist, seis, synth, rank, world, dev):
                          "kernel_variant_name": seis.search_variants()[chosen],
                          "autotune_ms_every_10th_item": [round(x, 3) for x in tune_ms]},
                         {"intersections_per_s": inter * world / (ms / 1e3),
+                         "roofline": roof,
                          "one_launch_per_item_ms": per_item_ms,
                          "speedup_vs_one_launch_per_item": per_item_ms / ms},
-                        clk, args.steps)
+                        clk, 2 * args.steps)
 
 
 def run_refine(args, torch, dist, seis, synth, rank, world, dev):

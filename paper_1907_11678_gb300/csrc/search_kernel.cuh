@@ -30,6 +30,7 @@
 #pragma once
 #include <cfloat>
 #include <climits>
+#include <type_traits>
 #include "seis_dev.cuh"
 #include "seis_internal.h"
 
@@ -574,7 +575,7 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
         }
     };
     setup(t0);
-    for (int t = t0; t < t1; ++t) {
+    auto step = [&](int t, auto more) {
         int cI[kR];
         float cX[kR];
         f2_t cX2[kX2 ? kG : 1];
@@ -588,7 +589,7 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
             #pragma unroll
             for (int g = 0; g < kG; ++g) cX2[g] = sX2[g];
         }
-        setup(min(t + 1, t1 - 1));
+        if constexpr (decltype(more)::value) setup(t + 1);
         #pragma unroll
         for (int g = 0; g < kG; ++g) {
             if constexpr (CFG::kMode == kScalar) {
@@ -628,7 +629,12 @@ __device__ __forceinline__ void accum_run(Accum<W, CFG>& a, const TraceMeta* met
                 }
             }
         }
-    }
+    };
+    // four traces per loop iteration: the pipeline's registers rotate instead of being
+    // copied, and fewer loop branches; the run's last trace sets up nothing
+    #pragma unroll 4
+    for (int t = t0; t < t1 - 1; ++t) step(t, std::true_type{});
+    step(t1 - 1, std::false_type{});
     if constexpr (FAST) {
         #pragma unroll
         for (int r = 0; r < kR; ++r) a.cntv[r] += t1 - t0;

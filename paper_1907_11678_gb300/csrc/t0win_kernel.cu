@@ -114,7 +114,7 @@ __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0
         }
     };
     setup(t0);
-    for (int t = t0; t < t1; ++t) {
+    auto step = [&](int t, auto more) {
         int cI0[kTwR], cI1[kTwR];
         f2_t cX2[kTwR];
         #pragma unroll
@@ -125,7 +125,7 @@ __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0
             a.M0[r] += sO0[r] ? 1 : 0;
             a.M1[r] += sO1[r] ? 1 : 0;
         }
-        setup(min(t + 1, t1 - 1));
+        if constexpr (decltype(more)::value) setup(t + 1);
         #pragma unroll
         for (int r = 0; r < kTwR; ++r) {
             const f2_t f0 = pk2(smf[cI0[r]], smf[cI1[r]]);
@@ -134,7 +134,9 @@ __device__ __forceinline__ void tw_run(TwAccum& a, const TraceMeta* meta, int t0
             a.s2[r] = add2(a.s2[r], v2);
             a.e2[r] = fma2(v2, v2, a.e2[r]);
         }
-    }
+    };
+    for (int t = t0; t < t1 - 1; ++t) step(t, std::true_type{});
+    step(t1 - 1, std::false_type{});           // the run's last trace sets up nothing
 }
 
 // Window sums of the output time at position p = lane + 32 h (h = 0, 1) of the 64-row
