@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
                 break;
             }
             int nfit = 0;
-            unsigned allv = 0u;                 // unused: every pair is checked
+            unsigned allv = 0u;
             const int ntr = produce_stage<true, HW>(sm.buf[slot], (int)(sm.buf[slot] - smf),
                                                     sm.meta[slot], &sm.full[slot], P.traces,
                                                     P.trace_off, P.h, P.m, P.list, lbeg,
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
                                                     nfit, allv);
             pl_t += nfit;
             done = pl_t >= M;
-            if (lane == 0) sm.desc[slot] = make_desc(0, ntr, 0u, 0, 0, 0);
+            if (lane == 0) sm.desc[slot] = make_desc(0, ntr, allv, 0, 0, 0);
             __syncwarp();
             mbar_arrive(&sm.full[slot]);
         }
@@ -144,7 +144,6 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
     }
     bool aborted = false;
     const f2_t shift2 = pk2(kFloorShift, kFloorShift);
-    const f2_t two2 = pk2(2.f, 2.f);
 
     for (int s = 0;; ++s) {
         const int slot = s % kPairSlots;
@@ -160,7 +159,12 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
             break;
         }
         const int ntr = min(d.ntr, kChunkT);
-        for (int t = 0; t < ntr; ++t) {
+        // One staged trace.  FAST: the producer found that every row and operator of the CTA
+        // takes part (window inside the trace, t0 + A dm >= 1e-3 and t^2 >= 1 sample^2 over
+        // the operators' box), so the participation tests, the selects and the guard on
+        // sqrt(t^2) + p are left out; the results are those of the checked form.
+        auto trace = [&](int t, auto fast) {
+            constexpr bool FAST = decltype(fast)::value;
             const TraceConst tc = trace_const(sm.meta[slot][t], n);
             // traveltime of both operators (the single kernel's operations, lane-wise)
             const f2_t e2 = tc.e2;
@@ -174,29 +178,48 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
             const float sua = sqrt_fast(ra), sub = sqrt_fast(rb);
             float sa, sb;
             up2(add2(pk2(sua, sub), pp2), sa, sb);
-            const f2_t D2 = fma2(rr2, pk2(rcp_fast(fmaxf(sa, 1e-30f)), rcp_fast(fmaxf(sb, 1e-30f))),
-                                 a2);
+            if constexpr (!FAST) {
+                sa = fmaxf(sa, 1e-30f);
+                sb = fmaxf(sb, 1e-30f);
+            }
+            const f2_t D2 = fma2(rr2, pk2(rcp_fast(sa), rcp_fast(sb)), a2);
             const f2_t t2 = add2_rm(D2, shift2);
-            float ta, tb, xa, xb;
+            float ta, tb;
             up2(t2, ta, tb);
-            up2(sub2(D2, sub2(t2, shift2)), xa, xb);
+            f2_t x2 = sub2(D2, sub2(t2, shift2));
             const int kka = __float_as_int(ta) + tc.off;
             const int kkb = __float_as_int(tb) + tc.off;
-            const bool oka = pa >= 0.f && (unsigned)kka <= tc.rng;
-            const bool okb = pb >= 0.f && (unsigned)kkb <= tc.rng;
-            const f2_t x2 = pk2(oka ? xa : 0.f, okb ? xb : 0.f);
-            const int ia = oka ? tc.kbase + kka : zidx;
-            const int ib = okb ? tc.kbase + kkb : zidx;
-            cnta += oka ? 1 : 0;
-            cntb += okb ? 1 : 0;
-            // du/d(A, B, C) of both operators
-            const f2_t ru2 = pk2((oka && sua > 0.f) ? rcp_fast(sua) : 0.f,
-                                 (okb && sub > 0.f) ? rcp_fast(sub) : 0.f);
-            const float hg = 0.5f * tc.g, hq = 0.5f * tc.q;
+            int ia, ib;
+            f2_t ru2;
+            if constexpr (FAST) {
+                // kk is clamped only to keep the reads of rows past the owner's end inside
+                // the staged window (their sums are discarded)
+                ia = tc.kbase + (int)min((unsigned)kka, tc.rng);
+                ib = tc.kbase + (int)min((unsigned)kkb, tc.rng);
+                ru2 = pk2(rcp_fast(sua), rcp_fast(sub));
+            } else {
+                const bool oka = pa >= 0.f && (unsigned)kka <= tc.rng;
+                const bool okb = pb >= 0.f && (unsigned)kkb <= tc.rng;
+                float xa, xb;
+                up2(x2, xa, xb);
+                x2 = pk2(oka ? xa : 0.f, okb ? xb : 0.f);
+                ia = oka ? tc.kbase + kka : zidx;
+                ib = okb ? tc.kbase + kkb : zidx;
+                cnta += oka ? 1 : 0;
+                cntb += okb ? 1 : 0;
+                ru2 = pk2((oka && sua > 0.f) ? rcp_fast(sua) : 0.f,
+                          (okb && sub > 0.f) ? rcp_fast(sub) : 0.f);
+            }
+            // du/d(A, B, C) of both operators, B's and C's taken at twice the single kernel's
+            // (g ru and q ru instead of 0.5 g ru and 0.5 q ru): that is the factor 2 their
+            // energy terms need, and their numerator sums come out doubled, which the end
+            // accounts for exactly (v (2 dnum) = (2 v) dnum).  A's energy term is summed
+            // without its factor 2 and doubled once after the loop (x + x, exact).  Powers of
+            // two only, so every output is still bit-identical to the single kernel's.
             f2_t du[3];
             du[0] = mul2(mul2(pp2, e2), ru2);
-            du[1] = mul2(pk2(hg, hg), ru2);
-            du[2] = mul2(pk2(hq, hq), ru2);
+            du[1] = mul2(tc.g2, ru2);
+            du[2] = mul2(tc.q2, ru2);
             float FA[W + 1], FB[W + 1];
             #pragma unroll
             for (int j = 0; j <= W; ++j) { FA[j] = smf[ia + j]; FB[j] = smf[ib + j]; }
@@ -213,11 +236,27 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
                 for (int a = 0; a < 3; ++a) dnum[a][j] = fma2(dj, du[a], dnum[a][j]);
             }
             #pragma unroll
-            for (int a = 0; a < 3; ++a) dden[a] = fma2(mul2(two2, du[a]), vd, dden[a]);
+            for (int a = 0; a < 3; ++a) dden[a] = fma2(du[a], vd, dden[a]);
+        };
+        int t = 0;
+        while (t < ntr) {                      // runs of check-free / checked traces
+            const bool fast = (d.allv >> t) & 1u;
+            const unsigned rest = (fast ? ~d.allv : d.allv) >> t;
+            const int len = rest ? __ffs(rest) - 1 : 32;
+            const int t1 = min(ntr, t + len);
+            if (fast) {
+                for (int u = t; u < t1; ++u) trace(u, std::true_type{});
+                cnta += t1 - t;
+                cntb += t1 - t;
+            } else {
+                for (int u = t; u < t1; ++u) trace(u, std::false_type{});
+            }
+            t = t1;
         }
         mbar_arrive(&sm.empty[slot]);
     }
     if (aborted || !act) return;
+    dden[0] = add2(dden[0], dden[0]);                // A's energy term: the factor 2
 
     // Eq. 1, the stack and dS per operator, in the single kernel's order
     #pragma unroll
@@ -231,10 +270,13 @@ __global__ void __launch_bounds__(kPairThreads, kPairCTAs) eval_pair_kernel(cons
             const float v = k ? hi : lo;
             nu = fmaf(v, v, nu);
             ac += v;
+            // B's and C's dnum hold twice the single kernel's sums: 2 v dnum = v (2 dnum)
+            up2(dnum[0][j], lo, hi);
+            dnu[0] = fmaf(2.f * v, k ? hi : lo, dnu[0]);
             #pragma unroll
-            for (int a = 0; a < 3; ++a) {
+            for (int a = 1; a < 3; ++a) {
                 up2(dnum[a][j], lo, hi);
-                dnu[a] = fmaf(2.f * v, k ? hi : lo, dnu[a]);
+                dnu[a] = fmaf(v, k ? hi : lo, dnu[a]);
             }
         }
         float dl, dh;
