@@ -441,9 +441,10 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
     ap = seis.crs_aperture(g, central, ds["apm"])
     A, B, C = _crs_grids(seis, dev, synth, 21, 21, 41)
     inter = int((ap.nbr_off[1:] - ap.nbr_off[:-1]).sum().item()) * 1500 * 21 * 21 * 41
-    # autotune on a 4-central slice in the same shape bucket (candidates, rows, fold)
+    # autotune on a 6-central slice in the same shape bucket (candidates, rows, fold): 282
+    # CTAs, about one wave with two CTAs on most SMs, as in the full run
     if args.variant is None:
-        apt = seis.crs_aperture(g, ds["central"][:4], ds["apm"])
+        apt = seis.crs_aperture(g, ds["central"][:6], ds["apm"])
         chosen, tune_ms = seis.autotune_crs(g, apt, A, B, C, w=W, reps=1)
     else:
         seis.autotune_clear()
@@ -485,7 +486,7 @@ def run_crs_line(args, torch, dist, seis, synth, rank, world, dev):
                                      "+-10 CMPs (1008 traces), 1500 samples @4ms, 21x21x41, w=11",
                          "intersections_per_step": inter * world, "kernel_variant": chosen,
                          "kernel_variant_name": seis.search_variants()[chosen],
-                         "autotune_ms_4_centrals": [round(x, 3) for x in tune_ms],
+                         "autotune_ms_6_centrals": [round(x, 3) for x in tune_ms],
                          "split_candidates_over_ctas": bool(split)},
                         {"intersections_per_s": inter * world / (ms / 1e3),
                          "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
@@ -738,7 +739,7 @@ def run_t0win(args, torch, dist, seis, synth, rank, world, dev):
     gc = seis.to_device(dc, dev)
     ap = seis.crs_aperture(gc, dc["central"][:64], dc["apm"])
     A, B, Cc = _crs_grids(seis, dev, synth, 21, 21, 41)
-    apt = seis.crs_aperture(gc, dc["central"][:4], dc["apm"])
+    apt = seis.crs_aperture(gc, dc["central"][:6], dc["apm"])
     seis.autotune_crs(gc, apt, A, B, Cc, w=W, reps=1)
     seis.crs_semblance_t0win(gc, ap, A, B, Cc, w=W)
     torch.cuda.synchronize()

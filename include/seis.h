@@ -394,7 +394,7 @@ int seis_batch_semblance(const seis_gathers* d, const seis_batch_item* items, in
 
 /* Autotuner of the batched search (no counterpart in the paper): runs the persistent
  * launch of seis_batch_semblance once untimed and `reps` times between CUDA events with each
- * variant the batch kernel is built for (0, 1, 3, 4, 9), records the fastest for the
+ * variant the batch kernel is built for (0, 1, 3, 4, 9, 10), records the fastest for the
  * window length w (later seis_batch_semblance calls with that w use it) and returns it in
  * *chosen (host, may be NULL).  ms_out (host, seis_search_variant_count() floats, may be
  * NULL) receives each tried variant's mean time and -1 for the others.  SYNCHRONOUS.

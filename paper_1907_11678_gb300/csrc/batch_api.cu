@@ -15,10 +15,11 @@ cudaError_t launch_batch_v1(const BatchParams&, int, int, cudaStream_t);
 cudaError_t launch_batch_v3(const BatchParams&, int, int, cudaStream_t);
 cudaError_t launch_batch_v4(const BatchParams&, int, int, cudaStream_t);
 cudaError_t launch_batch_v9(const BatchParams&, int, int, cudaStream_t);
+cudaError_t launch_batch_v10(const BatchParams&, int, int, cudaStream_t);
 
-// The batch kernel is instantiated for five of the search variants (its per-task state
-// costs registers, so the hybrid shapes are left out); any other choice maps to variant 3.
-static const int kBatchVariants[] = {0, 1, 3, 4, 9};
+// The batch kernel is instantiated for six of the search variants (its per-task state
+// costs registers, so most hybrid shapes are left out); any other choice maps to variant 3.
+static const int kBatchVariants[] = {0, 1, 3, 4, 9, 10};
 int batch_variant_of(int v) {
     for (int b : kBatchVariants)
         if (b == v) return v;
@@ -31,6 +32,7 @@ cudaError_t launch_batch(const BatchParams& p, int w, int grid, cudaStream_t s) 
         case 1: return launch_batch_v1(p, w, grid, s);
         case 4: return launch_batch_v4(p, w, grid, s);
         case 9: return launch_batch_v9(p, w, grid, s);
+        case 10: return launch_batch_v10(p, w, grid, s);
         default: return launch_batch_v3(p, w, grid, s);
     }
 }

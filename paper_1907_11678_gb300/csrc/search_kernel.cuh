@@ -933,6 +933,10 @@ using SearchV6 = SearchCfg<11, 2, kHybridV>;
 using SearchV7 = SearchCfg<15, 2, kHybridV>;
 using SearchV8 = SearchCfg<7, 4, kHybridD>;
 using SearchV9 = SearchCfg<7, 4, kHybridV>;
-constexpr int kSearchVariants = 10;
+// 12 consumer warps and the producer: warp w runs on warp scheduler w mod 4, so each of the
+// four schedulers holds three consumer warps of the CTA (the 15-warp shapes leave one with
+// two and the producer, and its warps run ahead of the others' and wait)
+using SearchV10 = SearchCfg<12, 2, kPacked>;
+constexpr int kSearchVariants = 11;
 
 }  // namespace seis

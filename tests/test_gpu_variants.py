@@ -145,7 +145,7 @@ def test_crs_line_slice_in_the_benchmark_configuration(seis):
     ap = seis.crs_aperture(g, central, ds["apm"])
     seis.autotune_clear()
     try:
-        apt = seis.crs_aperture(g, ds["central"][:4], ds["apm"])
+        apt = seis.crs_aperture(g, ds["central"][:6], ds["apm"])
         chosen, _ = seis.autotune_crs(g, apt, t(A), t(B), t(C), w=11, reps=1)
         print(f"[parity] crs-line variant {chosen}: {seis.search_variants()[chosen]}")
         got = _host(seis.crs_semblance(g, ap, t(A), t(B), t(C), w=11))
