@@ -11,22 +11,26 @@
 //   - one CTA = one owner (CMP gather or CRS central CDP) x 32 consecutive output rows;
 //     lane l of every consumer warp owns row n0 + l, so the 32 lanes of a warp read 32
 //     nearby sample indices of the same trace (conflict-free, often broadcast);
-//   - candidates are processed in passes of 28; a consumer thread keeps 4 candidates'
-//     accumulators (num[w], den, N) in registers through the whole trace loop, as two
-//     packed pairs updated with Blackwell's fma/add.rn.f32x2 (two FP32 lanes per issue);
+//   - candidates are processed in passes of NWARP x R (SearchCfg; 30 for the 15-warp
+//     shapes); a consumer thread keeps R candidates' accumulators (num[w], den, N) in
+//     registers through the whole trace loop, in packed pairs updated with Blackwell's
+//     fma/add.rn.f32x2 (two FP32 lanes per issue) or in scalar FP32;
 //   - a dedicated producer warp streams, per pass, the traces through a 4-slot
 //     shared-memory ring in stages of up to 32 traces: for every trace it computes the
-//     exact sample window the stage's 32 rows x 28 candidates can touch (traveltime
-//     bounds at the box corners, +-2 samples of margin) and copies it with one 1-D bulk
-//     copy (cp.async.bulk) plus at most 3+3 scalar edge loads; "full" mbarriers count the
-//     bytes, "empty" mbarriers return the slot; no block-wide barrier in the loop;
+//     exact sample window the stage's 32 rows x the pass's candidates can touch
+//     (traveltime bounds at the box corners, +-2 samples of margin), copies it with one
+//     1-D bulk copy (cp.async.bulk) plus at most 3+3 scalar edge loads, and writes the
+//     trace's metadata in the form the consumers use (window index, k offset and range,
+//     geometry factors as ready f32x2 pairs); "full" mbarriers count the bytes, "empty"
+//     mbarriers return the slot; no block-wide barrier in the loop;
 //   - the traveltime is formed in sample units as u = n + D with the cancellation-free
 //     moveout D = C q / (sqrt(n^2 + C q) + n), q = (h/dt)^2 (CRS: D = a + r/(s + p)),
 //     which keeps the interpolation fraction accurate to ~1e-4 samples in FP32;
 //   - the inner loop is branch-free: a pair whose trace does not take part reads a
 //     zero strip and adds nothing;
-//   - the argmax over all candidates stays inside the CTA (register running best per
-//     thread, then a 7-way shared-memory reduction), so no atomics and no cube.
+//   - the argmax over all candidates stays inside the CTA (each thread's running best in
+//     its own entry of the shared reduction arrays, then a reduction over the consumer
+//     warps), so no atomics and no cube.
 #pragma once
 #include <cfloat>
 #include <climits>
