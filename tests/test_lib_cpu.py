@@ -120,6 +120,13 @@ def test_variant_selector(lib):
     assert lib.seis_set_search_variant(-1) == -1
     assert lib.seis_set_search_variant(0) == 0 and lib.seis_get_search_variant() == 0
     assert lib.seis_set_search_variant(default) == 0
+    # every variant has its own name; the scheduler-balanced 12-warp shape is among them
+    lib.seis_search_variant_name.restype = ctypes.c_char_p
+    lib.seis_search_variant_name.argtypes = [ctypes.c_int]
+    names = [lib.seis_search_variant_name(v).decode() for v in range(n)]
+    assert all(names) and len(set(names)) == n
+    assert lib.seis_search_variant_name(n).decode() == ""
+    assert any(nm.startswith("12 warps x 2 candidates, packed") for nm in names)
 
 
 def test_refine_starts_arguments_are_checked(lib):
